@@ -1,0 +1,373 @@
+"""Benchmark: atom-timesteps/s of the short-range MD hot path on one GB300.
+
+Workload (one line): the 864,000-atom LJ liquid (60^3 fcc cells, rho 0.8442,
+T 1.44, rc 2.5, skin 0.3, dt 0.005), mixed precision, velocity-Verlet NVE
+with in-graph list rebuilds.  One bench "step" is one MD time step of the
+whole path (drift, displacement check, conditional list rebuild, force +
+kick).  The working set (list ~0.3 GB + state) exceeds the 129 MB L2, so no
+L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per rank, torchrun); the path has no
+exchange step ("replicas only").  --impl reference times the CPU oracle
+(FP64 O(N^2)) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-timesteps/s on 1 GB300, mixed vs plain FP64 at stated error; % roofline"
+UNIT = "atom-timesteps/s"
+WORKLOAD = "lj_liquid_864000_rc2.5_mixed"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=60)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / rc 5.0 / EAM / batch side runs")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- distributed --
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- workloads --
+
+def make_lj(synth, cells, rc, prec, tpa=0):
+    from paper_1009_4330_gb300 import System
+    d = synth.config1(rc=rc, cells=cells)
+    s = System.lj(d["x"], d["v"], d["box"], cutoff=rc, skin=d["skin"], dt=d["dt"], mass=1.0, precision=prec,
+                  list="auto", tpa=tpa)
+    return s, d
+
+
+def time_steps(s, K, W, sampler_gpu=None):
+    import torch
+    s.step(W)
+    torch.cuda.synchronize()
+    i0 = s.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(sampler_gpu) if sampler_gpu is not None else None
+    if clocks:
+        clocks.__enter__()
+    torch.cuda.synchronize()
+    e0.record()
+    s.step(K)
+    e1.record()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.__exit__()
+    i1 = s.info()
+    ms = e0.elapsed_time(e1)
+    return ms, i0, i1, (clocks.summary() if clocks else None)
+
+
+def e2e_run(s, d, K):
+    """Same metric through the public API with host buffers: pinned H2D of x,
+    v, K steps, D2H of energies and the final x, v -- all inside the timer."""
+    import torch
+    from paper_1009_4330_gb300 import system as sysmod  # noqa: F401
+    n = d["x"].shape[0]
+    hx = torch.from_numpy(d["x"]).pin_memory()
+    hv = torch.from_numpy(d["v"]).pin_memory()
+    ox = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    ov = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    oe = torch.empty((1, 8), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dx = hx.to("cuda", non_blocking=True)
+    dv = hv.to("cuda", non_blocking=True)
+    s.set_state(x=dx, v=dv)
+    s.step(K)
+    ev = s.energy_virial()
+    x, v, _ = s.state()
+    oe.copy_(ev, non_blocking=True)
+    ox.copy_(x, non_blocking=True)
+    ov.copy_(v, non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 2 * n * 3 * 8
+    d2h = 2 * n * 3 * 8 + 8 * 8
+    return {"value": n * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+            "seconds": dt, "steps": K}
+
+
+def cpu_baseline(synth, cells, budget_s):
+    """The oracle (FP64 O(N^2)) on a bounded sample of the same workload:
+    forces of m atoms of the 864,000-atom liquid, each an O(N) sum over all
+    atoms -- one atom-timestep of work per sampled atom (the integration is
+    O(1) per atom and negligible)."""
+    import oracle
+    d = synth.config1(rc=2.5, cells=cells)
+    n = d["x"].shape[0]
+    rng = np.random.default_rng(7)
+    m = 8
+    idx = rng.choice(n, m, replace=False)
+    t0 = time.perf_counter()
+    oracle.lj_at(d["x"], d["box"], 2.5, idx)
+    t1 = time.perf_counter() - t0
+    m2 = int(max(8, min(200000, m * budget_s / max(t1, 1e-6))))
+    idx = rng.choice(n, m2, replace=False)
+    t0 = time.perf_counter()
+    oracle.lj_at(d["x"], d["box"], 2.5, idx)
+    t2 = time.perf_counter() - t0
+    return {"value": m2 / t2, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"forces on {m2} random atoms of the {n}-atom LJ liquid (rc 2.5), FP64 O(N) each, "
+                      f"{t2:.1f} s"}
+
+
+# ------------------------------------------------------------------- arms --
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    cells = args.cells
+    d = synth.config1(rc=2.5, cells=cells)
+    n = d["x"].shape[0]
+    rng = np.random.default_rng(11)
+    # size each step's sample so that warmup + steps fit in ~2 minutes
+    probe = rng.choice(n, 4, replace=False)
+    t0 = time.perf_counter()
+    oracle.lj_at(d["x"], d["box"], 2.5, probe)
+    per_atom = (time.perf_counter() - t0) / 4
+    total = max(1, args.steps + args.warmup)
+    m = int(max(1, min(5000, 100.0 / total / max(per_atom, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.lj_at(d["x"], d["box"], 2.5, rng.choice(n, m, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.lj_at(d["x"], d["box"], 2.5, rng.choice(n, m, replace=False))
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "sample_atoms_per_step": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"each step: FP64 O(N) forces on {m} random atoms of the {n}-atom liquid"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import synth
+    torch.cuda.set_device(local)
+    dist = dist_init(ws)
+    cells = args.cells
+    s, d = make_lj(synth, cells, 2.5, "mixed", tpa=0)  # tpa 0: set-up mini-benchmark picks the layout
+    n = d["x"].shape[0]
+    K, W = args.steps, max(3, args.warmup)
+    barrier(dist)
+    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local)
+    ms = max_over_ranks(dist, ms)
+    value = ws * n * K / (ms / 1000.0)
+    rebuilds = i1["rebuilds"] - i0["rebuilds"]
+    # our kernels in the timed region: loop control once, per step the drift and
+    # the force pass (1 kernel full list, 3 half list), 6 per list rebuild
+    launches = 1 + K * (1 + (3 if i1["list"] == "half" else 1)) + 6 * rebuilds
+    # dominant kernel: the force pass as md_step runs it, timed with CUDA events on the handle's stream
+    f_ms, f_bytes = s.time_force(warmup=3, reps=20)
+    peak, peak_kind = load_peaks()
+    achieved = f_bytes / (f_ms / 1000.0) / 1e9
+    info = s.info()
+    e2e = e2e_run(s, d, K)
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = side_runs(synth, cells, K, W)
+    cpu = cpu_baseline(synth, cells, args.cpu_seconds) if (rank == 0 and ws == 1) else None
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair math, f64 accumulate/integrate", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "cells": cells, "rc": 2.5, "skin": 0.3, "dt": 0.005,
+                       "precision": "mixed", "tpa": info["tpa"], "list": info["list"], "block": info["block"],
+                       "avg_list_length": info["list_entries"] / n, "rebuilds_in_timed_region": rebuilds,
+                       "steps_per_rebuild": (K / rebuilds) if rebuilds else None,
+                       "l2": "working set > L2 (list alone ~0.3 GB): no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_lj (force + kick, md_step form)", "peak_kind": peak_kind,
+                         "force_ms": f_ms, "force_algorithmic_bytes": f_bytes,
+                         "force_share_of_step": f_ms / (ms / K)},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def side_runs(synth, cells, K, W):
+    """Context numbers: plain FP64 on the same workload, rc 5.0, EAM, batched replicas."""
+    import torch
+    from paper_1009_4330_gb300 import System, lj_params
+    out = {}
+    # plain FP64 GPU path, same workload
+    s, d = make_lj(synth, cells, 2.5, "fp64", tpa=0)
+    k = max(20, K // 10)
+    ms, i0, i1, _ = time_steps(s, k, 3)
+    n = d["x"].shape[0]
+    out["fp64_rc2.5"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"]}
+    s.close()
+    # rc 5.0, mixed
+    s, d = make_lj(synth, cells, 5.0, "mixed", tpa=0)
+    k = max(50, K // 4)
+    ms, i0, i1, _ = time_steps(s, k, 5)
+    fms, fby = s.time_force(3, 10)
+    out["mixed_rc5.0"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"],
+                          "force_GBs": fby / (fms / 1000) / 1e9}
+    s.close()
+    # EAM 500,000 atoms, mixed
+    e = synth.config2()
+    s = System.eam(e["x"], e["v"], e["box"], eam_params=e["eam"], skin=e["skin"], dt=e["dt"], mass=e["mass"],
+                   ftm2v=e["ftm2v"], precision="mixed", tpa=0)
+    k = max(50, K // 2)
+    ms, i0, i1, _ = time_steps(s, k, 5)
+    fms, fby = s.time_force(3, 10)
+    out["eam500000_mixed"] = {"value": e["x"].shape[0] * k / (ms / 1000), "steps": k, "tpa": i1["tpa"],
+                              "force_GBs": fby / (fms / 1000) / 1e9}
+    s.close()
+    # batched replicas (512, log-uniform 500..20000), mixed
+    b = synth.config4()
+    s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
+                     precision="mixed", tpa=0)
+    k = max(50, K // 4)
+    ms, i0, i1, _ = time_steps(s, k, 5)
+    nb = int(sum(b["sizes"]))
+    fms, fby = s.time_force(3, 10)
+    out["batch512_mixed"] = {"value": nb * k / (ms / 1000), "atoms": nb, "steps": k, "tpa": i1["tpa"],
+                             "force_GBs": fby / (fms / 1000) / 1e9}
+    s.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

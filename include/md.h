@@ -1,0 +1,235 @@
+/*
+ * md.h -- C ABI of the GB300 short-range molecular-dynamics hot path.
+ *
+ * One GPU, one process.  A handle owns a system -- or a batch of independent
+ * replicas -- resident in device memory: positions, velocities, forces,
+ * per-type coefficients, the cell-binned Verlet neighbour list and the CUDA
+ * graphs that advance it.  What the library computes follows Trott,
+ * Winterfeld & Crozier, "General-purpose molecular dynamics simulations on
+ * GPU-based clusters":
+ *   - pair forces summed over each atom's neighbour list, with a thread group
+ *     of 1..32 threads per atom (Sec. III.B: thread-per-atom and
+ *     block-per-atom, generalised; the group size is chosen by a timed
+ *     mini-benchmark at set-up, Sec. III.B);
+ *   - the cut-off Lennard-Jones ("lj/cut") and EAM potentials of App. A;
+ *   - double, or mixed precision: pair arithmetic in single precision while
+ *     time integration stays in double (Sec. II);
+ *   - NVE time integration on the GPU with no host round trips (Sec. II).
+ *
+ * Conventions, for every entry point unless stated otherwise:
+ *   - Arrays passed in or out are DEVICE pointers unless marked "host".
+ *     Positions, velocities and forces are row-major [n][3] doubles in the
+ *     caller's ORIGINAL atom order (the library keeps its own cell-sorted
+ *     order internally).  For a batch handle they are the replicas' arrays
+ *     concatenated in replica order.
+ *   - Ownership: the library copies every input it keeps; it owns all its
+ *     internal buffers; outputs go to caller-allocated memory.  The caller
+ *     must keep output buffers alive until the stream work completes.
+ *   - Asynchrony: work is enqueued on md_config.stream (a cudaStream_t;
+ *     NULL = legacy default stream).  Entry points that must read a device
+ *     value (md_create, md_step's list-overflow recovery, md_sync_status,
+ *     md_autotune, md_info) synchronise that stream.  Errors found on the
+ *     device (non-finite state, list overflow, wait time-outs) are latched in
+ *     a device status word and returned by the next md_sync_status.
+ *   - Errors: every entry point returns an md_status; md_last_error() gives
+ *     a one-line message for the most recent failure on that handle (or the
+ *     most recent handle-less failure when called with NULL).
+ *   - Thread safety: a handle must not be used by two host threads at once.
+ *   - Box: orthorhombic, periodic, origin 0.  Every edge must be at least
+ *     2 * (cutoff + skin), else MD_ERR_BOX_TOO_SMALL.
+ *   - Size limits: at most 2^26 atoms per handle (list entries carry a
+ *     26-bit atom index), at most MD_MAX_TYPES atom types.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_MAX_TYPES 8
+
+typedef struct md_system md_system; /* opaque, library-owned */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID = 1,        /* bad argument or configuration                         */
+    MD_ERR_CUDA = 2,           /* a CUDA runtime call failed                            */
+    MD_ERR_OOM = 3,            /* device allocation failed                              */
+    MD_ERR_BOX_TOO_SMALL = 4,  /* a box edge < 2 (cutoff + skin)                        */
+    MD_ERR_LIST_OVERFLOW = 5,  /* neighbour capacity exceeded and growing it failed     */
+    MD_ERR_NONFINITE = 6,      /* a position, velocity or force became NaN/Inf          */
+    MD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                    */
+    MD_ERR_UNSUPPORTED = 8     /* valid request outside this build's limits             */
+} md_status;
+
+typedef enum { MD_POT_LJ = 0, MD_POT_EAM_FS = 1 } md_potential;
+typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 } md_precision;
+typedef enum { MD_LIST_AUTO = 0, MD_LIST_FULL = 1, MD_LIST_HALF = 2 } md_listkind;
+
+typedef struct {
+    int64_t n_atoms;        /* atoms in this system (or replica)                              */
+    int32_t n_types;        /* 1..MD_MAX_TYPES                                                */
+    double box[3];          /* periodic edges Lx, Ly, Lz                                      */
+    md_potential pot;
+    const double *params;   /* host, copied.  LJ: eps[nt*nt] then sigma[nt*nt] (symmetric,    */
+                            /* row-major).  EAM_FS: {rc, A, c0, c1, c2}: rho(r) = (rc-r)^2,    */
+                            /* F(rho) = -A sqrt(rho), phi(r) = (rc-r)^2 (c0 + c1 r + c2 r^2).  */
+    int32_t n_params;       /* LJ: 2*nt*nt; EAM_FS: 5                                         */
+    double cutoff;          /* force cut-off rc (EAM: must equal params[0])                    */
+    double skin;            /* list radius = cutoff + skin; rebuild when an atom has moved     */
+                            /* more than skin/2 since the last build                           */
+    double dt;              /* time step                                                       */
+    const double *mass;     /* host, copied: mass[n_types]                                     */
+    double ftm2v;           /* acceleration = ftm2v * force / mass (1 in LJ units;             */
+                            /* 9.64853321e-3 for eV, Angstrom, amu, fs)                        */
+    int32_t energy_shift;   /* LJ only: 1 = report U(r) - U(rc); forces are unaffected         */
+    md_precision prec;      /* FP64, or MIXED (FP32 pair math; FP64 positions, velocities,     */
+                            /* integration and list cut-off test; compensated FP32 per-atom    */
+                            /* accumulation folded into FP64)                                  */
+    md_listkind list;       /* FULL (no atomics), HALF (Newton-3 with FP64 atomics), AUTO     */
+    int32_t tpa;            /* threads per atom 1,2,4,8,16,32; 0 = choose by mini-benchmark    */
+    void *stream;           /* cudaStream_t for all work of this handle                        */
+} md_config;
+
+/*
+ * Create a system from device arrays in original order: x[n][3] (any real
+ * coordinates; wrapped into the box), v[n][3], type[n] (0..n_types-1).
+ * Copies them, bins and sorts the atoms, builds the neighbour list and
+ * evaluates the initial forces.  Synchronises the stream.
+ * Cite: Sec. III.B (neighbour-list force approach), App. A (potentials).
+ */
+md_status md_create(const md_config *cfg, const double *x, const double *v, const int32_t *type,
+                    md_system **out);
+
+/*
+ * Create ONE handle advancing n_rep independent replicas together (batched
+ * replicas; each replica is its own periodic box).  cfgs[r] may differ in
+ * n_atoms and box only; every other field must equal cfgs[0].  x, v, type
+ * are host arrays of n_rep device pointers.  Every other entry point then
+ * acts on all replicas at once; per-replica outputs are concatenated in
+ * replica order.
+ */
+md_status md_batch_create(int32_t n_rep, const md_config *cfgs, const double *const *x,
+                          const double *const *v, const int32_t *const *type, md_system **out);
+
+/* Release the handle and all its device memory (synchronises its stream). */
+md_status md_destroy(md_system *h);
+
+/*
+ * Force a full list rebuild now: wrap, bin, counting-sort the atoms into bin
+ * order and rebuild every atom's neighbour set (all j with |x_i - x_j| <
+ * cutoff + skin, decided in double precision).  The list stays valid until
+ * an atom has moved skin/2.  Cite: Sec. III.B (numneigh[i], neighbors[i][jj]).
+ */
+md_status md_build_neighbors(md_system *h);
+
+/*
+ * Evaluate forces at the current positions (pair forces over the list,
+ * Sec. III.B listings) and store them; if f_out != NULL also write them to
+ * f_out[n][3] in original order.
+ */
+md_status md_compute_forces(md_system *h, double *f_out);
+
+/*
+ * Advance nsteps velocity-Verlet NVE steps entirely on the device
+ * (Sec. II: integration in double precision on the GPU).  Each step checks
+ * the displacement criterion and rebuilds the list inside the same CUDA
+ * graph when needed (no host round trip).  If a rebuild overflows the list
+ * capacity, the library grows it and resumes from the interrupted step
+ * (this case synchronises); MD_ERR_LIST_OVERFLOW only if growing fails.
+ */
+md_status md_step(md_system *h, int64_t nsteps);
+
+/*
+ * Potential energy, kinetic energy and virial at the current state:
+ * out[8*r + k] for replica r, k = {Epot, Ekin, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz}
+ * with W_ab = sum over pairs of d_a f_b (d = x_i - x_j).  Device pointer,
+ * 8 * n_rep doubles.  Summation order is fixed (deterministic).
+ */
+md_status md_energy_virial(md_system *h, double *out);
+
+/* Read the state in original order: x (wrapped into [0, L)), v, f -- any may be NULL. */
+md_status md_get_state(md_system *h, double *x, double *v, double *f);
+
+/* Replace positions and velocities (original order; either may be NULL), rebuild, recompute forces. */
+md_status md_set_state(md_system *h, const double *x, const double *v);
+
+/* Replace the potential parameters (host, layout of md_config.params); takes effect for the next force. */
+md_status md_set_params(md_system *h, const double *params);
+
+/*
+ * Backward pass of the LJ forces for a force-matching loss: given grad_f =
+ * dL/dF ([n][3], original order), write grad_x = dL/dx ([n][3], original
+ * order) and grad_params = dL/dparams (device, 2*nt*nt doubles in the
+ * layout of md_config.params; eps_ab is one parameter shared by the (a,b)
+ * and (b,a) entries and both entries receive its derivative).  The
+ * derivative is taken at fixed list: pairs at exactly r = rc contribute
+ * nothing.  Pair terms and sums are in double precision in both modes.
+ * grad_x or grad_params may be NULL.  Uses the current neighbour list.
+ * LJ only (MD_ERR_UNSUPPORTED otherwise).
+ */
+md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x, double *grad_params);
+
+/*
+ * Pick threads-per-atom, list kind and block size by timing the force pass
+ * (the paper's set-up mini-benchmark, Sec. III.B), then rebuild for the
+ * winner.  cache_path (host string, may be NULL) names a text file of
+ * earlier choices keyed by potential, precision, size and list length.
+ */
+md_status md_autotune(md_system *h, const char *cache_path);
+
+/* Select the force-kernel variant directly: tpa in {1,2,4,8,16,32}, list FULL or HALF, block 64..1024. */
+md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block);
+
+typedef struct {
+    int64_t n_atoms;         /* total real atoms                                          */
+    int32_t n_rep;           /* replicas                                                  */
+    int32_t tpa;             /* current threads per atom                                  */
+    int32_t list;            /* current md_listkind (FULL or HALF)                        */
+    int32_t block;           /* threads per block of the force kernel                     */
+    int32_t maxneigh;        /* list capacity per atom                                    */
+    int32_t max_count;       /* largest list length at the last build                     */
+    int64_t list_entries;    /* total list entries at the last build                      */
+    int64_t rebuilds;        /* list builds since creation                                */
+    int64_t steps;           /* time steps taken since creation                           */
+    int32_t bins[3];         /* bins per axis (replica 0)                                 */
+} md_info_t;
+
+/*
+ * Time the force pass exactly as md_step runs it (same kernels, list and
+ * threads per atom; velocities read and written) but with a zero kick, so
+ * the state is unchanged: `reps` launches bracketed by CUDA events on the
+ * handle's stream, after `warmup` untimed ones.  ms_out (host) receives the
+ * average milliseconds per force pass; bytes_out (host, may be NULL) the
+ * algorithmic DRAM bytes of one pass: list entries actually present (4 B
+ * each) plus, per atom, its record, list length and velocity in and out.
+ * For measurement only; the paper has no counterpart.  Synchronises.
+ */
+md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_out, double *bytes_out);
+
+/* Statistics (synchronises). */
+md_status md_info(md_system *h, md_info_t *out);
+
+/*
+ * Copy the neighbour list out, for inspection and testing: counts[n] and
+ * nbr[n][cap] (row-major; entries beyond counts[i] unspecified) in ORIGINAL
+ * atom indices (within the replica for a batch).  Full list: every j with
+ * |d_ij| < cutoff + skin at the last build; half list: each pair once.
+ * Device pointers.  MD_ERR_INVALID if cap < the largest count.
+ */
+md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t cap);
+
+/* Synchronise the handle's stream and return (and clear) the latched device status. */
+md_status md_sync_status(md_system *h);
+
+/* Message for the most recent failure on h (NULL: the last failure without a handle). */
+const char *md_last_error(md_system *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

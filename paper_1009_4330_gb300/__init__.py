@@ -1,0 +1,13 @@
+"""GB300-native short-range molecular dynamics hot path.
+
+Cut-off Lennard-Jones and Finnis-Sinclair EAM forces over cell-binned Verlet
+neighbour lists, the list rebuild and velocity-Verlet NVE integration, as
+hand-written CUDA for sm_103a behind the C ABI in include/md.h (libmd.so).
+After Trott, Winterfeld & Crozier, "General-purpose molecular dynamics
+simulations on GPU-based clusters" (LAMMPS_CUDA).
+"""
+from ._build import build as build_library  # noqa: F401
+from ._lib import load as load_library  # noqa: F401
+from .system import LJForces, MDError, System, lj_params, pairs_to_matrix  # noqa: F401
+
+__all__ = ["System", "LJForces", "MDError", "lj_params", "pairs_to_matrix", "build_library", "load_library"]

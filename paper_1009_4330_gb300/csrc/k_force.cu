@@ -1,0 +1,610 @@
+// k_force.cu -- pair-force kernels over the Verlet list (LJ full and half
+// list, EAM density and force passes), the drift and kick kernels of
+// velocity Verlet, and the md_step loop control.
+//
+// Force loop (paper Sec. III.B): a group of T threads owns atom i
+// (T = 1 is the paper's thread-per-atom, T = 32 a warp-per-atom form of its
+// block-per-atom); thread `sub` of the group walks list entries sub, sub+T,
+// ..., gathers j's record, evaluates the pair term and accumulates; the group
+// then reduces its partial sums with warp shuffles (the paper's reduce(ftmp)
+// of the block-per-atom listing) and one thread writes atom i.
+// Per-type coefficient tables are staged in shared memory.
+//
+// Precision (paper Sec. II, mixed mode: force in single, integration in
+// double): MIXED gathers FP32 cell-relative records, does the pair
+// arithmetic in FP32, accumulates each thread's partial sums with Kahan
+// compensation and folds them into FP64 for the group reduction, kick and
+// store.  FP64 does everything in double.
+#include "md_common.cuh"
+#include "md_kernels.h"
+
+namespace md {
+
+// ------------------------------------------------------ precision policy --
+
+template <int PREC>
+struct Pol;
+
+template <>
+struct Pol<MD_PREC_MIXED> {
+    using real = float;
+    using Acc = KahanF;
+    __device__ static __forceinline__ void load(const View &V, int j, float &x, float &y, float &z, int &t) {
+        const float4 r = __ldg(&V.rec[j]);
+        x = r.x; y = r.y; z = r.z; t = __float_as_int(r.w);
+    }
+    __device__ static __forceinline__ float h(const Rep &R, int c) { return R.hf[c]; }
+    __device__ static __forceinline__ float rcp(float x) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    __device__ static __forceinline__ float fp(const View &V, int j) { return __ldg(&V.fp32[j]); }
+};
+
+struct AccD {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double y) { s += y; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Pol<MD_PREC_FP64> {
+    using real = double;
+    using Acc = AccD;
+    __device__ static __forceinline__ void load(const View &V, int j, double &x, double &y, double &z, int &t) {
+        const double4_32a q = V.pos4[j];
+        x = q.x; y = q.y; z = q.z; t = (int)__double_as_longlong(q.w);
+    }
+    __device__ static __forceinline__ double h(const Rep &R, int c) { return R.h[c]; }
+    __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+    __device__ static __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+    __device__ static __forceinline__ double fp(const View &V, int j) { return V.fp64[j]; }
+};
+
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// reduce a double over the T consecutive lanes of a group
+template <int T>
+__device__ __forceinline__ double group_sum(double x) {
+    for (int o = T / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Epilogue of atom p (after the group reduction), by the group's lane 0.
+//   kModeStoreF: F -> f.   kModeStep: v += c dt a with c = 1 (leapfrog full
+//   kick) or 1/2 (last step of the call, F also stored).   kModeEV: F -> f.
+__device__ __forceinline__ void epilogue(const View &V, int mode, int rem, int p, int t, double fx, double fy,
+                                         double fz, const double *s_ftm) {
+    const int n = V.n_pad;
+    if (mode == kModeStep || mode == kModeKickDry) {
+        const bool last = (mode == kModeStep && rem == 1);
+        const double c = (mode == kModeKickDry) ? 0.0 : (last ? 0.5 : 1.0) * V.dt * s_ftm[t];
+        V.v[p] += c * fx;
+        V.v[n + p] += c * fy;
+        V.v[2 * n + p] += c * fz;
+        if (last) {
+            V.f[p] = fx; V.f[n + p] = fy; V.f[2 * n + p] = fz;
+        }
+    } else {
+        V.f[p] = fx; V.f[n + p] = fy; V.f[2 * n + p] = fz;
+    }
+}
+
+__device__ __forceinline__ void write_ev(const View &V, int p, int t, double e, const double *w, const double *s_ftm) {
+    const int n = V.n_pad;
+    const double vx = V.v[p], vy = V.v[n + p], vz = V.v[2 * n + p];
+    V.ev[p] = e;
+    V.ev[n + p] = 0.5 * (vx * vx + vy * vy + vz * vz) / s_ftm[t];
+    for (int k = 0; k < 6; ++k) V.ev[(2 + k) * n + p] = w[k];
+}
+
+// md_step bookkeeping by the last block of the step's final kernel
+__device__ __forceinline__ void finish_step(const View &V, const KArgs &a) {
+    if (a.mode != kModeStep) return;
+    if (last_block(&V.ctl->ticket_force)) {
+        if (threadIdx.x == 0) {
+            V.ctl->ticket_force = 0;
+            const int rem = V.ctl->remaining - 1;
+            V.ctl->remaining = rem;
+            if (V.ctl->err == 0) V.ctl->steps += 1;
+            if (a.in_graph) cudaGraphSetConditional(V.cond_loop, (rem > 0 && V.ctl->err == 0) ? 1u : 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- LJ ----
+
+// FULL: every neighbour in i's list, F_i only, no atomics.
+// HALF: each pair once; F_j -= f_ij by FP64 atomics, F_i += sum by one atomic
+//       per component at the end (F zeroed beforehand; kick in k_kick).
+template <int PREC, int T, int HALF, int EV, int MT>
+__global__ void __launch_bounds__(256) k_lj(View V, KArgs a) {
+    using P = Pol<PREC>;
+    using real = typename P::real;
+    __shared__ real s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
+    __shared__ real s_lj3[kMaxTypes * kMaxTypes], s_lj4[kMaxTypes * kMaxTypes], s_off[kMaxTypes * kMaxTypes];
+    __shared__ double s_ftm[kMaxTypes];
+    const int np = V.ntypes * V.ntypes;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        if (PREC == MD_PREC_FP64) {
+            s_lj1[k] = V.tab->lj1[k]; s_lj2[k] = V.tab->lj2[k];
+            s_lj3[k] = V.tab->lj3[k]; s_lj4[k] = V.tab->lj4[k]; s_off[k] = V.tab->off[k];
+        } else {
+            s_lj1[k] = V.tab->lj1f[k]; s_lj2[k] = V.tab->lj2f[k];
+            s_lj3[k] = V.tab->lj3f[k]; s_lj4[k] = V.tab->lj4f[k]; s_off[k] = V.tab->offf[k];
+        }
+    }
+    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    __syncthreads();
+
+    const unsigned err = V.ctl->err;
+    const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    const bool warp_in = (gw * A < V.n_pad) && err == 0;
+
+    typename P::Acc ax, ay, az;
+    ax.zero(); ay.zero(); az.zero();
+    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
+    bool valid = false;
+    int ti = 0;
+    if (warp_in) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            const int cnt = V.ncount[p];
+            real xi, yi, zi;
+            P::load(V, p, xi, yi, zi, ti);
+            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
+            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
+            const int maxn = V.maxneigh;
+            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
+            const int n = V.n_pad;
+            for (int k = sub; k < cnt; k += T, lp += 32) {
+                const uint32_t e = ld_stream(lp);
+                const int j = (int)(e & kIdxMask);
+                real xj, yj, zj;
+                int tj;
+                P::load(V, j, xj, yj, zj, tj);
+                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
+                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
+                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
+                const real r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2) {
+                    const int tp = MT ? ti * V.ntypes + tj : 0;
+                    const real r2i = P::rcp(r2);
+                    const real r6i = r2i * r2i * r2i;
+                    const real fpair = r6i * (s_lj1[tp] * r6i - s_lj2[tp]) * r2i;
+                    const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
+                    ax.add(fxp); ay.add(fyp); az.add(fzp);
+                    if (HALF) {
+                        atomicAdd(&V.f[j], -(double)fxp);
+                        atomicAdd(&V.f[n + j], -(double)fyp);
+                        atomicAdd(&V.f[2 * n + j], -(double)fzp);
+                    }
+                    if (EV) {
+                        const double wgt = HALF ? 1.0 : 0.5;
+                        e_acc += wgt * (double)(r6i * (s_lj3[tp] * r6i - s_lj4[tp]) - s_off[tp]);
+                        w_acc[0] += wgt * (double)(dx * fxp);
+                        w_acc[1] += wgt * (double)(dy * fyp);
+                        w_acc[2] += wgt * (double)(dz * fzp);
+                        w_acc[3] += wgt * (double)(dx * fyp);
+                        w_acc[4] += wgt * (double)(dx * fzp);
+                        w_acc[5] += wgt * (double)(dy * fzp);
+                    }
+                }
+            }
+        }
+    }
+    double fx = group_sum<T>(ax.value());
+    double fy = group_sum<T>(ay.value());
+    double fz = group_sum<T>(az.value());
+    if (EV) {
+        e_acc = group_sum<T>(e_acc);
+        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(w_acc[k]);
+    }
+    if (valid && sub == 0) {
+        if (HALF) {
+            const int n = V.n_pad;
+            atomicAdd(&V.f[p], fx);
+            atomicAdd(&V.f[n + p], fy);
+            atomicAdd(&V.f[2 * n + p], fz);
+            if (EV) {
+                V.ev[p] = e_acc;
+                for (int k = 0; k < 6; ++k) V.ev[(2 + k) * n + p] = w_acc[k];
+            }
+        } else {
+            epilogue(V, a.mode, rem, p, ti, fx, fy, fz, s_ftm);
+            if (EV) write_ev(V, p, ti, e_acc, w_acc, s_ftm);
+        }
+    }
+    if (!HALF) finish_step(V, a);
+}
+
+// zero F before a half-list pass
+__global__ void k_zero_f(View V, KArgs a) {
+    const int n3 = 3 * V.n_pad;
+    if (V.ctl->err) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) V.f[i] = 0.0;
+}
+
+// kick after a half-list pass (F complete): mode as in the force epilogue;
+// kModeEV adds the kinetic term
+__global__ void k_kick(View V, KArgs a) {
+    __shared__ double s_ftm[kMaxTypes];
+    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    __syncthreads();
+    const unsigned err = V.ctl->err;
+    const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < V.n_pad && err == 0) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        if (p - R.atom0 < R.natoms) {
+            const int n = V.n_pad;
+            const int t = V.type[p];
+            if (a.mode == kModeStep || a.mode == kModeKickDry) {
+                const double c = (a.mode == kModeKickDry) ? 0.0 : (rem == 1 ? 0.5 : 1.0) * V.dt * s_ftm[t];
+                V.v[p] += c * V.f[p];
+                V.v[n + p] += c * V.f[n + p];
+                V.v[2 * n + p] += c * V.f[2 * n + p];
+            } else if (a.mode == kModeEV) {
+                const double vx = V.v[p], vy = V.v[n + p], vz = V.v[2 * n + p];
+                V.ev[n + p] = 0.5 * (vx * vx + vy * vy + vz * vz) / s_ftm[t];
+            }
+        }
+    }
+    finish_step(V, a);
+}
+
+// --------------------------------------------------------------- EAM ----
+// Finnis-Sinclair analytic EAM (the paper's App. A EAM benchmark; form
+// rho = (rc-r)^2, F = -A sqrt(rho), phi = (rc-r)^2 (c0 + c1 r + c2 r^2)).
+
+// pass 1: host density rho_i = sum_j (rc - r)^2 and the embedding derivative
+// F'(rho_i) = -A / (2 sqrt(rho_i)) (0 at rho = 0), FP64 per atom
+template <int PREC, int T>
+__global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
+    using P = Pol<PREC>;
+    using real = typename P::real;
+    const unsigned err = V.ctl->err;
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    typename P::Acc acc;
+    acc.zero();
+    bool valid = false;
+    if (gw * A < V.n_pad && err == 0) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            const int cnt = V.ncount[p];
+            real xi, yi, zi;
+            int ti;
+            P::load(V, p, xi, yi, zi, ti);
+            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
+            const real rc = (PREC == MD_PREC_FP64) ? (real)V.tab->eam[0] : (real)V.tab->eamf[0];
+            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
+            const int maxn = V.maxneigh;
+            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
+            for (int k = sub; k < cnt; k += T, lp += 32) {
+                const uint32_t e = ld_stream(lp);
+                const int j = (int)(e & kIdxMask);
+                real xj, yj, zj;
+                int tj;
+                P::load(V, j, xj, yj, zj, tj);
+                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
+                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
+                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
+                const real r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2) {
+                    const real r = r2 * P::rsqrt(r2);
+                    const real t = rc - r;
+                    acc.add(t * t);
+                }
+            }
+        }
+    }
+    const double rho = group_sum<T>(acc.value());
+    if (valid && sub == 0) {
+        const double Aemb = V.tab->eam[1];
+        const double sr = sqrt(rho);
+        const double fpv = rho > 0.0 ? -0.5 * Aemb / sr : 0.0;
+        if (PREC == MD_PREC_FP64) V.fp64[p] = fpv;
+        else V.fp32[p] = (float)fpv;
+        if (a.mode == kModeEV) V.emb[p] = rho > 0.0 ? -Aemb * sr : 0.0;
+    }
+}
+
+// pass 2: F_i = -sum_j [phi'(r) + (F'_i + F'_j) rho'(r)] d / r
+template <int PREC, int T, int EV>
+__global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
+    using P = Pol<PREC>;
+    using real = typename P::real;
+    __shared__ double s_ftm[kMaxTypes];
+    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    __syncthreads();
+    const unsigned err = V.ctl->err;
+    const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    typename P::Acc ax, ay, az;
+    ax.zero(); ay.zero(); az.zero();
+    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
+    bool valid = false;
+    int ti = 0;
+    if (gw * A < V.n_pad && err == 0) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            const int cnt = V.ncount[p];
+            real xi, yi, zi;
+            P::load(V, p, xi, yi, zi, ti);
+            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
+            real rc, c0, c1, c2;
+            if (PREC == MD_PREC_FP64) {
+                rc = V.tab->eam[0]; c0 = V.tab->eam[2]; c1 = V.tab->eam[3]; c2 = V.tab->eam[4];
+            } else {
+                rc = V.tab->eamf[0]; c0 = V.tab->eamf[2]; c1 = V.tab->eamf[3]; c2 = V.tab->eamf[4];
+            }
+            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
+            const real fpi = P::fp(V, p);
+            const int maxn = V.maxneigh;
+            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
+            for (int k = sub; k < cnt; k += T, lp += 32) {
+                const uint32_t e = ld_stream(lp);
+                const int j = (int)(e & kIdxMask);
+                real xj, yj, zj;
+                int tj;
+                P::load(V, j, xj, yj, zj, tj);
+                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
+                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
+                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
+                const real r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2) {
+                    const real rinv = P::rsqrt(r2);
+                    const real r = r2 * rinv;
+                    const real t = rc - r;
+                    const real poly = c0 + r * (c1 + r * c2);
+                    const real dpoly = c1 + (real)2 * c2 * r;
+                    // -(phi' + (F'_i + F'_j) rho') / r with phi' = -2t poly + t^2 dpoly, rho' = -2t
+                    const real coef = -t * ((real)-2 * poly + t * dpoly - (real)2 * (fpi + P::fp(V, j))) * rinv;
+                    const real fxp = dx * coef, fyp = dy * coef, fzp = dz * coef;
+                    ax.add(fxp); ay.add(fyp); az.add(fzp);
+                    if (EV) {
+                        e_acc += 0.5 * (double)(t * t * poly);
+                        w_acc[0] += 0.5 * (double)(dx * fxp);
+                        w_acc[1] += 0.5 * (double)(dy * fyp);
+                        w_acc[2] += 0.5 * (double)(dz * fzp);
+                        w_acc[3] += 0.5 * (double)(dx * fyp);
+                        w_acc[4] += 0.5 * (double)(dx * fzp);
+                        w_acc[5] += 0.5 * (double)(dy * fzp);
+                    }
+                }
+            }
+        }
+    }
+    const double fx = group_sum<T>(ax.value());
+    const double fy = group_sum<T>(ay.value());
+    const double fz = group_sum<T>(az.value());
+    if (EV) {
+        e_acc = group_sum<T>(e_acc);
+        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(w_acc[k]);
+    }
+    if (valid && sub == 0) {
+        epilogue(V, a.mode, rem, p, ti, fx, fy, fz, s_ftm);
+        if (EV) write_ev(V, p, ti, e_acc + V.emb[p], w_acc, s_ftm);
+    }
+    finish_step(V, a);
+}
+
+// ------------------------------------------------------- drift + control --
+
+// x += dt v (after v += dt/2 a(F) on the first step of an md_step call);
+// refresh the FP32 record; per-replica max displacement since the build;
+// the last block turns it into per-replica rebuild flags and sets the
+// rebuild conditional of the step graph.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
+    __shared__ double s_ftm[kMaxTypes];
+    __shared__ float s_m[32];
+    __shared__ int s_r[32];
+    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    __syncthreads();
+    const unsigned err = V.ctl->err;
+    const int first = V.ctl->first;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = V.n_pad;
+    float d2 = 0.f;
+    int r = -1;
+    if (p < n) {
+        r = V.tile_rep[p >> 5];
+        const Rep &R = V.rep[r];
+        if (err == 0 && (p - R.atom0) < R.natoms) {
+            double x[3], v[3];
+            int t;
+            if (PREC == MD_PREC_FP64) {
+                const double4_32a q = V.pos4[p];
+                x[0] = q.x; x[1] = q.y; x[2] = q.z;
+                t = (int)__double_as_longlong(q.w);
+            } else {
+                for (int c = 0; c < 3; ++c) x[c] = V.xr[c * n + p];
+                t = V.type[p];
+            }
+            for (int c = 0; c < 3; ++c) v[c] = V.v[c * n + p];
+            if (first) {
+                const double hk = 0.5 * V.dt * s_ftm[t];
+                for (int c = 0; c < 3; ++c) {
+                    v[c] += hk * V.f[c * n + p];
+                    V.v[c * n + p] = v[c];
+                }
+            }
+            for (int c = 0; c < 3; ++c) x[c] += V.dt * v[c];
+            const float4 nr = make_float4((float)x[0], (float)x[1], (float)x[2], __int_as_float(t));
+            if (PREC == MD_PREC_FP64) {
+                V.pos4[p] = make_double4_32a(x[0], x[1], x[2], __longlong_as_double((long long)t));
+            } else {
+                for (int c = 0; c < 3; ++c) V.xr[c * n + p] = x[c];
+                V.rec[p] = nr;
+            }
+            const float4 b = V.recb[p];
+            const float ex = nr.x - b.x, ey = nr.y - b.y, ez = nr.z - b.z;
+            d2 = ex * ex + ey * ey + ez * ez;
+            if (!(d2 <= 3.0e38f)) d2 = __int_as_float(0x7f800000);  // NaN/Inf -> +Inf
+        }
+    }
+    const float wm = warp_max(d2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { s_m[w] = wm; s_r[w] = r; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cr = -1;
+        float cm = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            if (s_r[k] != cr) {
+                if (cr >= 0 && cm > 0.f) atomicMax(&V.rep_disp[cr], __float_as_uint(cm));
+                cr = s_r[k];
+                cm = 0.f;
+            }
+            cm = fmaxf(cm, s_m[k]);
+        }
+        if (cr >= 0 && cm > 0.f) atomicMax(&V.rep_disp[cr], __float_as_uint(cm));
+    }
+    if (last_block(&V.ctl->ticket_drift)) {
+        int any = 0;
+        bool bad = false;
+        for (int q = threadIdx.x; q < V.n_rep; q += blockDim.x) {
+            const unsigned m = V.rep_disp[q];
+            V.rep_disp[q] = 0u;
+            const bool nonfin = m >= 0x7f800000u;
+            const int flag = (nonfin || __uint_as_float(m) > V.skin_half2f) ? 1 : 0;
+            V.rep_flag[q] = flag;
+            any |= flag;
+            bad |= nonfin;
+        }
+        if (bad) latch_error(V.ctl, kErrNonfinite);
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) {
+            V.ctl->ticket_drift = 0;
+            V.ctl->first = 0;
+            if (a.in_graph) cudaGraphSetConditional(V.cond_rebuild, (any && V.ctl->err == 0) ? 1u : 0u);
+        }
+    }
+}
+
+// before the WHILE node: loop while steps remain and no error is latched
+__global__ void k_loop_init(View V, KArgs a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        cudaGraphSetConditional(V.cond_loop, (V.ctl->remaining > 0 && V.ctl->err == 0) ? 1u : 0u);
+}
+
+// ------------------------------------------------------------- dispatch ----
+
+template <int PREC, int HALF, int EV, int MT>
+static const void *pick_lj(int T) {
+    switch (T) {
+        case 1: return (const void *)k_lj<PREC, 1, HALF, EV, MT>;
+        case 2: return (const void *)k_lj<PREC, 2, HALF, EV, MT>;
+        case 4: return (const void *)k_lj<PREC, 4, HALF, EV, MT>;
+        case 8: return (const void *)k_lj<PREC, 8, HALF, EV, MT>;
+        case 16: return (const void *)k_lj<PREC, 16, HALF, EV, MT>;
+        default: return (const void *)k_lj<PREC, 32, HALF, EV, MT>;
+    }
+}
+
+template <int PREC>
+static const void *pick_lj_prec(int T, int half, int ev, int mt) {
+    if (half) {
+        if (ev) return mt ? pick_lj<PREC, 1, 1, 1>(T) : pick_lj<PREC, 1, 1, 0>(T);
+        return mt ? pick_lj<PREC, 1, 0, 1>(T) : pick_lj<PREC, 1, 0, 0>(T);
+    }
+    if (ev) return mt ? pick_lj<PREC, 0, 1, 1>(T) : pick_lj<PREC, 0, 1, 0>(T);
+    return mt ? pick_lj<PREC, 0, 0, 1>(T) : pick_lj<PREC, 0, 0, 0>(T);
+}
+
+template <int PREC>
+static const void *pick_rho(int T) {
+    switch (T) {
+        case 1: return (const void *)k_eam_rho<PREC, 1>;
+        case 2: return (const void *)k_eam_rho<PREC, 2>;
+        case 4: return (const void *)k_eam_rho<PREC, 4>;
+        case 8: return (const void *)k_eam_rho<PREC, 8>;
+        case 16: return (const void *)k_eam_rho<PREC, 16>;
+        default: return (const void *)k_eam_rho<PREC, 32>;
+    }
+}
+
+template <int PREC, int EV>
+static const void *pick_eamf(int T) {
+    switch (T) {
+        case 1: return (const void *)k_eam_force<PREC, 1, EV>;
+        case 2: return (const void *)k_eam_force<PREC, 2, EV>;
+        case 4: return (const void *)k_eam_force<PREC, 4, EV>;
+        case 8: return (const void *)k_eam_force<PREC, 8, EV>;
+        case 16: return (const void *)k_eam_force<PREC, 16, EV>;
+        default: return (const void *)k_eam_force<PREC, 32, EV>;
+    }
+}
+
+void force_sequence(const View &V, int mode, int block, bool in_graph, std::vector<KCall> &seq) {
+    KArgs a{};
+    a.mode = mode;
+    a.in_graph = in_graph ? 1 : 0;
+    const int T = V.tpa;
+    const int ev = (mode == kModeEV) ? 1 : 0;
+    const long long threads = (long long)V.n_pad * T;
+    const dim3 grid((unsigned)((threads + block - 1) / block));
+    const int fp64 = (V.prec == MD_PREC_FP64);
+    if (V.pot == MD_POT_LJ) {
+        const int mt = V.ntypes > 1 ? 1 : 0;
+        const void *fn = fp64 ? pick_lj_prec<MD_PREC_FP64>(T, V.half, ev, mt)
+                              : pick_lj_prec<MD_PREC_MIXED>(T, V.half, ev, mt);
+        if (V.half) {
+            seq.push_back(KCall{(const void *)k_zero_f, dim3((3 * V.n_pad + 255) / 256), dim3(256), 0, a});
+            KArgs af = a;
+            af.mode = kModeStoreF;
+            af.in_graph = 0;
+            seq.push_back(KCall{fn, grid, dim3(block), 0, af});
+            seq.push_back(KCall{(const void *)k_kick, dim3((V.n_pad + 255) / 256), dim3(256), 0, a});
+        } else {
+            seq.push_back(KCall{fn, grid, dim3(block), 0, a});
+        }
+    } else {
+        KArgs ar = a;
+        ar.in_graph = 0;
+        seq.push_back(KCall{fp64 ? pick_rho<MD_PREC_FP64>(T) : pick_rho<MD_PREC_MIXED>(T), grid, dim3(block), 0, ar});
+        const void *fn = fp64 ? (ev ? pick_eamf<MD_PREC_FP64, 1>(T) : pick_eamf<MD_PREC_FP64, 0>(T))
+                              : (ev ? pick_eamf<MD_PREC_MIXED, 1>(T) : pick_eamf<MD_PREC_MIXED, 0>(T));
+        seq.push_back(KCall{fn, grid, dim3(block), 0, a});
+    }
+}
+
+void drift_sequence(const View &V, bool in_graph, std::vector<KCall> &seq) {
+    KArgs a{};
+    a.in_graph = in_graph ? 1 : 0;
+    seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_drift<MD_PREC_FP64>
+                                               : (const void *)k_drift<MD_PREC_MIXED>,
+                        dim3((V.n_pad + 255) / 256), dim3(256), 0, a});
+}
+
+void loop_init_sequence(const View &V, std::vector<KCall> &seq) {
+    KArgs a{};
+    a.in_graph = 1;
+    seq.push_back(KCall{(const void *)k_loop_init, dim3(1), dim3(32), 0, a});
+}
+
+}  // namespace md

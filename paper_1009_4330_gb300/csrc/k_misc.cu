@@ -1,0 +1,334 @@
+// k_misc.cu -- moving state between the caller's original order and the
+// library's cell-sorted order, deterministic energy/virial reduction, the LJ
+// backward (vector-Jacobian) kernel, and list export.
+#include "md_common.cuh"
+#include "md_kernels.h"
+
+namespace md {
+
+// ------------------------------------------------------------------ I/O ----
+
+// Stage replica r's caller arrays (x, v, type of that replica alone, original
+// order) into the rebuild scratch: atom `local` goes to slot atom0 + local.
+__global__ void k_stage_in(View V, int r, const double *x, const double *v, const int *type) {
+    const int local = blockIdx.x * blockDim.x + threadIdx.x;
+    const Rep &R = V.rep[r];
+    if (local >= R.natoms) return;
+    const int p = R.atom0 + local;
+    const int n = V.n_pad;
+    for (int c = 0; c < 3; ++c) {
+        V.tx[c * n + p] = x[3 * (size_t)local + c];
+        V.tv[c * n + p] = v[3 * (size_t)local + c];
+    }
+    V.ttype[p] = type[local];
+    V.tid[p] = local;
+}
+
+// absolute position of sorted slot p from its cell-relative coordinates
+template <int PREC>
+__device__ __forceinline__ void abs_pos(const View &V, const Rep &R, int p, double x[3]) {
+    const int b = V.bpk[p];
+    const int bc[3] = {unpack_bx(b), unpack_by(b), unpack_bz(b)};
+    if (PREC == MD_PREC_FP64) {
+        const double4_32a q = V.pos4[p];
+        x[0] = q.x; x[1] = q.y; x[2] = q.z;
+    } else {
+        for (int c = 0; c < 3; ++c) x[c] = V.xr[c * V.n_pad + p];
+    }
+    for (int c = 0; c < 3; ++c) x[c] += ((double)bc[c] + 0.5) * R.h[c];
+}
+
+// Stage new positions and/or velocities (original order; NULL keeps the
+// current value) together with the current types and ids, for a full rebuild.
+template <int PREC>
+__global__ void k_restage(View V, const double *x, const double *v) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.n_pad) return;
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    if (p - R.atom0 >= R.natoms) return;
+    const int n = V.n_pad;
+    const int id = V.id[p];
+    const int d = R.atom0 + id;
+    const long long o = R.orig0 + id;
+    double xa[3];
+    abs_pos<PREC>(V, R, p, xa);
+    for (int c = 0; c < 3; ++c) {
+        V.tx[c * n + d] = x ? x[3 * o + c] : xa[c];
+        V.tv[c * n + d] = v ? v[3 * o + c] : V.v[c * n + p];
+    }
+    V.ttype[d] = V.type[p];
+    V.tid[d] = id;
+}
+
+template <int PREC>
+__global__ void k_state_out(View V, double *x, double *v, double *f) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.n_pad) return;
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    if (p - R.atom0 >= R.natoms) return;
+    const int n = V.n_pad;
+    const long long o = R.orig0 + V.id[p];
+    if (x) {
+        double xa[3];
+        abs_pos<PREC>(V, R, p, xa);
+        for (int c = 0; c < 3; ++c) {
+            const double L = R.L[c];
+            double w = xa[c] - floor(xa[c] * R.Linv[c]) * L;
+            if (w >= L) w -= L;
+            if (w < 0.0) w += L;
+            x[3 * o + c] = w;
+        }
+    }
+    if (v) for (int c = 0; c < 3; ++c) v[3 * o + c] = V.v[c * n + p];
+    if (f) for (int c = 0; c < 3; ++c) f[3 * o + c] = V.f[c * n + p];
+}
+
+// ------------------------------------------------------ energy / virial ----
+
+// out[8 r + k] = sum over replica r's atoms of ev[k][p], fixed order
+__global__ void k_ev_reduce(View V, double *out) {
+    __shared__ double s[8][256];
+    const int r = blockIdx.x;
+    const Rep &R = V.rep[r];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = R.atom0 + threadIdx.x; p < R.atom0 + R.natoms; p += blockDim.x)
+        for (int k = 0; k < 8; ++k) acc[k] += V.ev[k * V.n_pad + p];
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 8; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) out[8 * r + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// ------------------------------------------------------------- backward ----
+// Force-matching backward for LJ.  With L a function of the forces and
+// g = dL/dF:  dL/dx_i = sum_j M_ij (g_i - g_j),  M = s(r) I + (s'(r)/r) d d^T,
+// s = -U'(r)/r;  dL/deps_ab = sum_i g_i . sum_{j of pair type ab} s d / eps,
+// dL/dsig_ab = sum_i g_i . sum_j (ds/dsig) d.  Full list (both orders of each
+// pair), no atomics; pair terms and sums in FP64.
+
+__global__ void k_grad_in(View V, const double *grad_f) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.n_pad) return;
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    const int n = V.n_pad;
+    if (p - R.atom0 >= R.natoms) {
+        for (int c = 0; c < 3; ++c) V.gs[c * n + p] = 0.0;
+        return;
+    }
+    const long long o = R.orig0 + V.id[p];
+    for (int c = 0; c < 3; ++c) V.gs[c * n + p] = grad_f[3 * o + c];
+}
+
+template <int PREC>
+__device__ __forceinline__ void load64(const View &V, int j, double &x, double &y, double &z, int &t) {
+    if (PREC == MD_PREC_FP64) {
+        const double4_32a q = V.pos4[j];
+        x = q.x; y = q.y; z = q.z;
+        t = (int)__double_as_longlong(q.w);
+    } else {
+        const int n = V.n_pad;
+        x = V.xr[j]; y = V.xr[n + j]; z = V.xr[2 * n + j];
+        t = V.type[j];
+    }
+}
+
+template <int PREC, int T, int NTM>
+__global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
+    constexpr int NQ = NTM * NTM;
+    __shared__ double s_red[8][2 * NQ];
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    const int nt = V.ntypes;
+    const int n = V.n_pad;
+    double ge[NQ], gsg[NQ];
+    for (int q = 0; q < NQ; ++q) { ge[q] = 0.0; gsg[q] = 0.0; }
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    bool valid = false;
+    if (gw * A < n) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            const int cnt = V.ncount[p];
+            double xi, yi, zi;
+            int ti;
+            load64<PREC>(V, p, xi, yi, zi, ti);
+            const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
+            const int maxn = V.maxneigh;
+            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
+            for (int k = sub; k < cnt; k += T, lp += 32) {
+                const uint32_t e = *lp;
+                const int j = (int)(e & kIdxMask);
+                double xj, yj, zj;
+                int tj;
+                load64<PREC>(V, j, xj, yj, zj, tj);
+                const double dx = xi - xj - (double)code_delta(e, 26) * R.h[0];
+                const double dy = yi - yj - (double)code_delta(e, 28) * R.h[1];
+                const double dz = zi - zj - (double)code_delta(e, 30) * R.h[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < V.rc2)) continue;
+                const int tp = ti * nt + tj;
+                const double lj1 = V.tab->lj1[tp], lj2 = V.tab->lj2[tp];
+                const double r2i = 1.0 / r2, r6i = r2i * r2i * r2i;
+                const double s = r6i * (lj1 * r6i - lj2) * r2i;
+                const double spr = r6i * r2i * r2i * (-14.0 * lj1 * r6i + 8.0 * lj2);
+                const double dgx = gix - V.gs[j], dgy = giy - V.gs[n + j], dgz = giz - V.gs[2 * n + j];
+                const double ddg = dx * dgx + dy * dgy + dz * dgz;
+                gx += s * dgx + spr * dx * ddg;
+                gy += s * dgy + spr * dy * ddg;
+                gz += s * dgz + spr * dz * ddg;
+                const double gd = gix * dx + giy * dy + giz * dz;
+                const int ta = min(ti, tj), tb = max(ti, tj);
+                const int q = (NTM == 1) ? 0 : ta * NTM + tb;
+                const double sg = V.tab->sig[tp];
+                ge[q] += gd * s / V.tab->eps[tp];
+                gsg[q] += gd * (r2i * r6i / sg) * (12.0 * lj1 * r6i - 6.0 * lj2);
+            }
+        }
+    }
+    for (int o = T / 2; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    }
+    if (valid && sub == 0) {
+        V.gx[p] = gx; V.gx[n + p] = gy; V.gx[2 * n + p] = gz;
+    }
+    // parameter gradients: warp sums, then the block's warps in order
+    for (int q = 0; q < NQ; ++q) {
+        const double a1 = warp_sum(ge[q]), a2 = warp_sum(gsg[q]);
+        if (lane == 0) { s_red[w][q] = a1; s_red[w][NQ + q] = a2; }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < 2 * NQ) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k][threadIdx.x];
+        V.gp_part[(size_t)blockIdx.x * (2 * NQ) + threadIdx.x] = t;
+    }
+}
+
+// sum the per-block partials in block order and expand to the symmetric
+// (eps[nt*nt], sig[nt*nt]) layout
+template <int NTM>
+__global__ void k_gp_reduce(View V, int nblocks, double *grad_params) {
+    constexpr int NQ = NTM * NTM;
+    const int nt = V.ntypes;
+    const int t = threadIdx.x;
+    if (t >= 2 * NQ) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += V.gp_part[(size_t)b * (2 * NQ) + t];
+    const int which = t / NQ, q = t % NQ;
+    const int ta = (NTM == 1) ? 0 : q / NTM, tb = (NTM == 1) ? 0 : q % NTM;
+    if (ta > tb || ta >= nt || tb >= nt) return;
+    double *g = grad_params + which * nt * nt;
+    g[ta * nt + tb] = s;
+    g[tb * nt + ta] = s;
+}
+
+__global__ void k_grad_out(View V, double *grad_x) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.n_pad) return;
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    if (p - R.atom0 >= R.natoms) return;
+    const long long o = R.orig0 + V.id[p];
+    const int n = V.n_pad;
+    for (int c = 0; c < 3; ++c) grad_x[3 * o + c] = V.gx[c * n + p];
+}
+
+// ------------------------------------------------------------ list out ----
+
+__global__ void k_neighbors_out(View V, int *counts, int *nbr, int cap) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.n_pad) return;
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    if (p - R.atom0 >= R.natoms) return;
+    const long long o = R.orig0 + V.id[p];
+    const int c = V.ncount[p];
+    counts[o] = c;
+    for (int k = 0; k < c && k < cap; ++k) {
+        const uint32_t e = V.nlist[list_index(p, k, V.tpa, V.maxneigh)];
+        nbr[o * cap + k] = V.id[e & kIdxMask];
+    }
+}
+
+// ------------------------------------------------------------ launchers ----
+
+static dim3 grid_of(int n, int b) { return dim3((unsigned)((n + b - 1) / b)); }
+
+cudaError_t launch_stage_in(const View &V, int r, int natoms, const double *x, const double *v, const int *type,
+                            cudaStream_t s) {
+    k_stage_in<<<grid_of(natoms, 256), 256, 0, s>>>(V, r, x, v, type);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restage(const View &V, const double *x, const double *v, cudaStream_t s) {
+    if (V.prec == MD_PREC_FP64) k_restage<MD_PREC_FP64><<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, x, v);
+    else k_restage<MD_PREC_MIXED><<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, x, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_out(const View &V, double *x, double *v, double *f, cudaStream_t s) {
+    if (V.prec == MD_PREC_FP64) k_state_out<MD_PREC_FP64><<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, x, v, f);
+    else k_state_out<MD_PREC_MIXED><<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, x, v, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ev_reduce(const View &V, double *out, cudaStream_t s) {
+    k_ev_reduce<<<V.n_rep, 256, 0, s>>>(V, out);
+    return cudaGetLastError();
+}
+
+int backward_partial_blocks(const View &V) {
+    const long long threads = (long long)V.n_pad * V.tpa;
+    return (int)((threads + 255) / 256);
+}
+
+template <int PREC, int NTM>
+static const void *pick_bwd(int T) {
+    switch (T) {
+        case 1: return (const void *)k_lj_bwd<PREC, 1, NTM>;
+        case 2: return (const void *)k_lj_bwd<PREC, 2, NTM>;
+        case 4: return (const void *)k_lj_bwd<PREC, 4, NTM>;
+        case 8: return (const void *)k_lj_bwd<PREC, 8, NTM>;
+        case 16: return (const void *)k_lj_bwd<PREC, 16, NTM>;
+        default: return (const void *)k_lj_bwd<PREC, 32, NTM>;
+    }
+}
+
+cudaError_t launch_backward(const View &V, const double *grad_f, double *grad_x, double *grad_params, int nblocks,
+                            cudaStream_t s) {
+    k_grad_in<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, grad_f);
+    const int ntm = V.ntypes == 1 ? 1 : (V.ntypes == 2 ? 2 : kMaxTypes);
+    const void *fn;
+    if (V.prec == MD_PREC_FP64)
+        fn = ntm == 1 ? pick_bwd<MD_PREC_FP64, 1>(V.tpa) : ntm == 2 ? pick_bwd<MD_PREC_FP64, 2>(V.tpa)
+                                                                    : pick_bwd<MD_PREC_FP64, kMaxTypes>(V.tpa);
+    else
+        fn = ntm == 1 ? pick_bwd<MD_PREC_MIXED, 1>(V.tpa) : ntm == 2 ? pick_bwd<MD_PREC_MIXED, 2>(V.tpa)
+                                                                     : pick_bwd<MD_PREC_MIXED, kMaxTypes>(V.tpa);
+    KArgs a{};
+    View Vc = V;
+    void *args[2] = {(void *)&Vc, (void *)&a};
+    cudaError_t e = cudaLaunchKernel(fn, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    if (grad_params) {
+        if (ntm == 1) k_gp_reduce<1><<<1, 128, 0, s>>>(V, nblocks, grad_params);
+        else if (ntm == 2) k_gp_reduce<2><<<1, 128, 0, s>>>(V, nblocks, grad_params);
+        else k_gp_reduce<kMaxTypes><<<1, 128, 0, s>>>(V, nblocks, grad_params);
+    }
+    if (grad_x) k_grad_out<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, grad_x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbors_out(const View &V, int *counts, int *nbr, int cap, cudaStream_t s) {
+    k_neighbors_out<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, counts, nbr, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace md

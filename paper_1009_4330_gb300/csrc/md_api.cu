@@ -1,0 +1,844 @@
+// md_api.cu -- the C ABI (include/md.h): handle life cycle, device memory,
+// the md_step CUDA graph, list-overflow recovery and the set-up
+// mini-benchmark that picks threads per atom (paper Sec. III.B: both force
+// variants are kept and the faster one is chosen by a short timed test when
+// the simulation is set up).
+//
+// md_step graph (built once per handle configuration, replayed per call):
+//
+//   k_loop_init --> WHILE(cond_loop) {
+//       k_drift --> IF(cond_rebuild) { zero bins, prepare, scan, scatter,
+//                                      gather, build } --> force pass(es)
+//   }
+//
+// k_drift's last block sets cond_rebuild from the per-replica displacement
+// check; the force pass's last block decrements the remaining step count and
+// sets cond_loop.  No host round trip per step.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "md_common.cuh"
+#include "md_kernels.h"
+
+using namespace md;
+
+struct md_system {
+    View V{};
+    md_config cfg{};
+    std::vector<double> params;
+    std::vector<double> mass;
+    cudaStream_t s = nullptr;
+    int n_rep = 0;
+    long long n_real = 0;
+    std::vector<Rep> reps;
+    std::vector<void *> allocs;
+    PairTab *d_tab = nullptr;
+    Ctl *d_ctl = nullptr;
+    int block = 256;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t gp_part_size = 0;
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+static md_status fail(md_system *h, md_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    g_err = buf;
+    return st;
+}
+
+#define CK(h, call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+    } while (0)
+
+template <class T>
+static cudaError_t dalloc(md_system *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e == cudaSuccess) h->allocs.push_back((void *)*p);
+    return e;
+}
+
+static void dfree(md_system *h, void *p) {
+    if (!p) return;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(p);
+}
+
+static void drop_graph(md_system *h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+}
+
+// ------------------------------------------------------------- launches --
+
+static cudaError_t run_seq(md_system *h, const std::vector<KCall> &seq) {
+    for (const KCall &k : seq) {
+        View Vc = h->V;
+        KArgs a = k.args;
+        a.in_graph = 0;
+        void *args[2] = {(void *)&Vc, (void *)&a};
+        cudaError_t e = cudaLaunchKernel(k.fn, k.grid, k.block, args, k.smem, h->s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t add_chain(md_system *h, cudaGraph_t g, const std::vector<KCall> &seq, cudaGraphNode_t *dep,
+                             cudaGraphNode_t *last) {
+    cudaGraphNode_t prev = dep ? *dep : nullptr;
+    for (const KCall &k : seq) {
+        View Vc = h->V;
+        KArgs a = k.args;
+        void *args[2] = {(void *)&Vc, (void *)&a};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)k.fn;
+        kp.gridDim = k.grid;
+        kp.blockDim = k.block;
+        kp.sharedMemBytes = (unsigned)k.smem;
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e != cudaSuccess) return e;
+        prev = node;
+    }
+    *last = prev;
+    return cudaSuccess;
+}
+
+static cudaError_t add_conditional(cudaGraph_t g, cudaGraphNode_t *dep, cudaGraphConditionalHandle hnd,
+                                   cudaGraphConditionalNodeType type, cudaGraphNode_t *node, cudaGraph_t *body) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaSuccess;
+}
+
+static md_status build_step_graph(md_system *h) {
+    drop_graph(h);
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    h->graph = g;
+    cudaGraphConditionalHandle hloop, hreb;
+    CK(h, cudaGraphConditionalHandleCreate(&hloop, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    CK(h, add_conditional(g, nullptr, hloop, cudaGraphCondTypeWhile, &wnode, &body));
+    CK(h, cudaGraphConditionalHandleCreate(&hreb, body, 0, cudaGraphCondAssignDefault));
+    h->V.cond_loop = hloop;
+    h->V.cond_rebuild = hreb;
+    // top level: loop init -> WHILE
+    std::vector<KCall> seq;
+    loop_init_sequence(h->V, seq);
+    cudaGraphNode_t init_last;
+    CK(h, add_chain(h, g, seq, nullptr, &init_last));
+    CK(h, cudaGraphAddDependencies(g, &init_last, &wnode, nullptr, 1));
+    // body: drift -> IF(rebuild) -> force
+    seq.clear();
+    drift_sequence(h->V, true, seq);
+    cudaGraphNode_t drift_last;
+    CK(h, add_chain(h, body, seq, nullptr, &drift_last));
+    cudaGraphNode_t inode;
+    cudaGraph_t rbody;
+    CK(h, add_conditional(body, &drift_last, hreb, cudaGraphCondTypeIf, &inode, &rbody));
+    seq.clear();
+    rebuild_sequence(h->V, false, false, seq);
+    for (auto &k : seq) k.args.in_graph = 1;
+    cudaGraphNode_t rlast;
+    CK(h, add_chain(h, rbody, seq, nullptr, &rlast));
+    seq.clear();
+    force_sequence(h->V, kModeStep, h->block, true, seq);
+    cudaGraphNode_t flast;
+    CK(h, add_chain(h, body, seq, &inode, &flast));
+    CK(h, cudaGraphInstantiate(&h->exec, g, 0));
+    return MD_OK;
+}
+
+// ---------------------------------------------------------- host helpers --
+
+static md_status read_ctl(md_system *h, Ctl *c) {
+    CK(h, cudaMemcpyAsync(c, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    return MD_OK;
+}
+
+static md_status alloc_list(md_system *h, int maxn) {
+    dfree(h, h->V.nlist);
+    h->V.nlist = nullptr;
+    h->V.maxneigh = maxn;
+    CK(h, dalloc(h, &h->V.nlist, (size_t)h->V.n_pad * (size_t)maxn));
+    drop_graph(h);
+    return MD_OK;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// run the list build kernel again (after growing the list)
+static md_status rebuild_list_only(md_system *h, bool all) {
+    std::vector<KCall> seq;
+    rebuild_sequence(h->V, all, false, seq);
+    std::vector<KCall> last(seq.end() - 1, seq.end());  // k_build
+    CK(h, run_seq(h, last));
+    return MD_OK;
+}
+
+// After a build: grow the list and rebuild while it overflowed.
+static md_status settle_overflow(md_system *h, bool all) {
+    for (int it = 0; it < 8; ++it) {
+        Ctl c;
+        md_status st = read_ctl(h, &c);
+        if (st) return st;
+        if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity");
+        if (!(c.err & kErrOverflow)) return MD_OK;
+        const int need = round_up((int)std::ceil(c.need_maxneigh * 1.2) + 8, 32);
+        st = alloc_list(h, need);
+        if (st) return st;
+        unsigned zero = 0;
+        int zi = 0;
+        CK(h, cudaMemcpyAsync(&h->d_ctl->err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, h->s));
+        CK(h, cudaMemcpyAsync(&h->d_ctl->need_maxneigh, &zi, sizeof(int), cudaMemcpyHostToDevice, h->s));
+        st = rebuild_list_only(h, all);
+        if (st) return st;
+    }
+    return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list still overflowing after growing");
+}
+
+static md_status full_rebuild(md_system *h, bool staged) {
+    std::vector<KCall> seq;
+    rebuild_sequence(h->V, true, staged, seq);
+    CK(h, run_seq(h, seq));
+    return settle_overflow(h, true);
+}
+
+static md_status compute_forces(md_system *h, int mode) {
+    std::vector<KCall> seq;
+    force_sequence(h->V, mode, h->block, false, seq);
+    CK(h, run_seq(h, seq));
+    return MD_OK;
+}
+
+static void fill_tab(md_system *h, PairTab &t) {
+    std::memset(&t, 0, sizeof(t));
+    const int nt = h->cfg.n_types;
+    const double rc = h->cfg.cutoff;
+    if (h->cfg.pot == MD_POT_LJ) {
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nt; ++b) {
+                const int p = a * nt + b;
+                const double e = h->params[p], s = h->params[nt * nt + p];
+                const double s6 = std::pow(s, 6.0), s12 = s6 * s6;
+                t.eps[p] = e;
+                t.sig[p] = s;
+                t.lj1[p] = 48.0 * e * s12;
+                t.lj2[p] = 24.0 * e * s6;
+                t.lj3[p] = 4.0 * e * s12;
+                t.lj4[p] = 4.0 * e * s6;
+                const double sr6 = s6 / std::pow(rc, 6.0);
+                t.off[p] = h->cfg.energy_shift ? 4.0 * e * (sr6 * sr6 - sr6) : 0.0;
+                t.lj1f[p] = (float)t.lj1[p];
+                t.lj2f[p] = (float)t.lj2[p];
+                t.lj3f[p] = (float)t.lj3[p];
+                t.lj4f[p] = (float)t.lj4[p];
+                t.offf[p] = (float)t.off[p];
+            }
+    } else {
+        for (int k = 0; k < 5; ++k) {
+            t.eam[k] = h->params[k];
+            t.eamf[k] = (float)h->params[k];
+        }
+    }
+    for (int a = 0; a < nt; ++a) t.ftm_m[a] = h->cfg.ftm2v / h->mass[a];
+}
+
+static md_status upload_tab(md_system *h) {
+    PairTab t;
+    fill_tab(h, t);
+    CK(h, cudaMemcpyAsync(h->d_tab, &t, sizeof(PairTab), cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    return MD_OK;
+}
+
+static md_status check_cfg(const md_config *c) {
+    if (!c) return fail(nullptr, MD_ERR_INVALID, "null config");
+    if (c->n_atoms <= 0) return fail(nullptr, MD_ERR_INVALID, "n_atoms must be positive");
+    if (c->n_types < 1 || c->n_types > kMaxTypes) return fail(nullptr, MD_ERR_INVALID, "n_types out of range");
+    if (c->pot != MD_POT_LJ && c->pot != MD_POT_EAM_FS) return fail(nullptr, MD_ERR_INVALID, "unknown potential");
+    if (c->prec != MD_PREC_FP64 && c->prec != MD_PREC_MIXED) return fail(nullptr, MD_ERR_INVALID, "unknown precision");
+    if (!c->params || !c->mass) return fail(nullptr, MD_ERR_INVALID, "params and mass are required");
+    if (c->pot == MD_POT_LJ && c->n_params != 2 * c->n_types * c->n_types)
+        return fail(nullptr, MD_ERR_INVALID, "LJ needs 2*n_types^2 params");
+    if (c->pot == MD_POT_EAM_FS) {
+        if (c->n_params != 5) return fail(nullptr, MD_ERR_INVALID, "EAM_FS needs 5 params");
+        if (c->n_types != 1) return fail(nullptr, MD_ERR_UNSUPPORTED, "EAM_FS is single-element");
+        if (c->params[0] != c->cutoff) return fail(nullptr, MD_ERR_INVALID, "EAM rc (params[0]) must equal cutoff");
+    }
+    if (!(c->cutoff > 0) || !(c->skin >= 0) || !(c->dt > 0) || !(c->ftm2v > 0))
+        return fail(nullptr, MD_ERR_INVALID, "cutoff, dt, ftm2v must be positive, skin >= 0");
+    for (int t = 0; t < c->n_types; ++t)
+        if (!(c->mass[t] > 0)) return fail(nullptr, MD_ERR_INVALID, "masses must be positive");
+    const double rl = c->cutoff + c->skin;
+    for (int a = 0; a < 3; ++a)
+        if (!(c->box[a] >= 2.0 * rl))
+            return fail(nullptr, MD_ERR_BOX_TOO_SMALL, "box edge %g < 2 (cutoff + skin) = %g", c->box[a], 2 * rl);
+    if (c->tpa != 0 && c->tpa != 1 && c->tpa != 2 && c->tpa != 4 && c->tpa != 8 && c->tpa != 16 && c->tpa != 32)
+        return fail(nullptr, MD_ERR_INVALID, "tpa must be 0,1,2,4,8,16 or 32");
+    if (c->list != MD_LIST_AUTO && c->list != MD_LIST_FULL && c->list != MD_LIST_HALF)
+        return fail(nullptr, MD_ERR_INVALID, "unknown list kind");
+    if (c->list == MD_LIST_HALF && c->pot != MD_POT_LJ)
+        return fail(nullptr, MD_ERR_UNSUPPORTED, "half lists are implemented for LJ only");
+    return MD_OK;
+}
+
+static bool same_shared(const md_config &a, const md_config &b) {
+    if (a.n_types != b.n_types || a.pot != b.pot || a.n_params != b.n_params || a.cutoff != b.cutoff ||
+        a.skin != b.skin || a.dt != b.dt || a.ftm2v != b.ftm2v || a.energy_shift != b.energy_shift ||
+        a.prec != b.prec || a.list != b.list || a.tpa != b.tpa || a.stream != b.stream)
+        return false;
+    for (int k = 0; k < a.n_params; ++k)
+        if (a.params[k] != b.params[k]) return false;
+    for (int k = 0; k < a.n_types; ++k)
+        if (a.mass[k] != b.mass[k]) return false;
+    return true;
+}
+
+// first guess at the list capacity: 1.4 x the ideal-gas count at the densest replica
+static int initial_maxneigh(const std::vector<Rep> &reps, double rl) {
+    double rho = 0;
+    for (const Rep &r : reps) rho = std::max(rho, r.natoms / (r.L[0] * r.L[1] * r.L[2]));
+    const double n = 4.18879020478639 * rl * rl * rl * rho;
+    return round_up((int)std::ceil(1.4 * n) + 16, 32);
+}
+
+static md_status create_impl(int n_rep, const md_config *cfgs, const double *const *x, const double *const *v,
+                             const int32_t *const *type, md_system **out) {
+    if (!out) return fail(nullptr, MD_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    if (n_rep < 1) return fail(nullptr, MD_ERR_INVALID, "n_rep must be >= 1");
+    for (int r = 0; r < n_rep; ++r) {
+        md_status st = check_cfg(&cfgs[r]);
+        if (st) return st;
+        if (r > 0 && !same_shared(cfgs[0], cfgs[r]))
+            return fail(nullptr, MD_ERR_INVALID, "replica %d differs from replica 0 beyond n_atoms/box", r);
+        if (!x[r] || !v[r] || !type[r]) return fail(nullptr, MD_ERR_INVALID, "null x/v/type for replica %d", r);
+    }
+    md_system *h = new md_system();
+    h->cfg = cfgs[0];
+    h->params.assign(cfgs[0].params, cfgs[0].params + cfgs[0].n_params);
+    h->mass.assign(cfgs[0].mass, cfgs[0].mass + cfgs[0].n_types);
+    h->cfg.params = h->params.data();
+    h->cfg.mass = h->mass.data();
+    h->s = (cudaStream_t)cfgs[0].stream;
+    h->n_rep = n_rep;
+    const double rl = h->cfg.cutoff + h->cfg.skin;
+    int atom0 = 0, bin0 = 0, tile0 = 0;
+    long long orig0 = 0;
+    for (int r = 0; r < n_rep; ++r) {
+        Rep R{};
+        for (int a = 0; a < 3; ++a) {
+            R.L[a] = cfgs[r].box[a];
+            R.Linv[a] = 1.0 / R.L[a];
+            int nb = (int)std::floor(R.L[a] / rl);
+            while (nb > 1 && R.L[a] / nb < rl) --nb;
+            nb = std::min(std::max(nb, 2), kMaxBinsPerAxis);
+            R.nb[a] = nb;
+            R.h[a] = R.L[a] / nb;
+            R.hinv[a] = nb / R.L[a];
+            R.hf[a] = (float)R.h[a];
+        }
+        R.nbins = R.nb[0] * R.nb[1] * R.nb[2];
+        R.bin0 = bin0;
+        R.natoms = (int)cfgs[r].n_atoms;
+        R.atom0 = atom0;
+        R.tile0 = tile0;
+        R.ntiles = (R.natoms + 31) / 32;
+        R.orig0 = orig0;
+        atom0 += R.ntiles * 32;
+        tile0 += R.ntiles;
+        bin0 += R.nbins;
+        orig0 += cfgs[r].n_atoms;
+        if ((long long)atom0 > kMaxAtoms) {
+            delete h;
+            return fail(nullptr, MD_ERR_UNSUPPORTED, "more than 2^26 atoms");
+        }
+        h->reps.push_back(R);
+    }
+    h->n_real = orig0;
+    View &V = h->V;
+    V.n_pad = atom0;
+    V.n_tiles = tile0;
+    V.n_rep = n_rep;
+    V.nbins_total = bin0;
+    V.prec = h->cfg.prec;
+    V.pot = h->cfg.pot;
+    V.ntypes = h->cfg.n_types;
+    V.half = (h->cfg.list == MD_LIST_HALF) ? 1 : 0;
+    V.tpa = h->cfg.tpa ? h->cfg.tpa : 1;
+    V.dt = h->cfg.dt;
+    V.rc2 = h->cfg.cutoff * h->cfg.cutoff;
+    V.rl2 = rl * rl;
+    V.skin_half2 = 0.25 * h->cfg.skin * h->cfg.skin;
+    V.rc2f = (float)V.rc2;
+    // FP32 list test margin: 1e-4 rl^2, ~50x the worst FP32 error of |d|^2
+    V.rl2f_lo = (float)(V.rl2 * (1.0 - 1e-4));
+    V.rl2f_hi = (float)(V.rl2 * (1.0 + 1e-4));
+    V.skin_half2f = (float)V.skin_half2;
+
+    const size_t n = (size_t)V.n_pad;
+    auto bail = [&](cudaError_t e) {
+        md_status st = fail(nullptr, e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA, "allocation: %s",
+                            cudaGetErrorString(e));
+        md_destroy(h);
+        return st;
+    };
+#define AL(ptr, cnt)                            \
+    do {                                        \
+        cudaError_t e_ = dalloc(h, &(ptr), cnt); \
+        if (e_ != cudaSuccess) return bail(e_); \
+    } while (0)
+    Rep *d_rep;
+    int *d_tile_rep;
+    AL(d_rep, (size_t)n_rep);
+    AL(d_tile_rep, (size_t)V.n_tiles);
+    V.rep = d_rep;
+    V.tile_rep = d_tile_rep;
+    AL(V.rep_disp, (size_t)n_rep);
+    AL(V.rep_flag, (size_t)n_rep);
+    if (V.prec == MD_PREC_FP64) AL(V.pos4, n);
+    else AL(V.xr, 3 * n);
+    AL(V.v, 3 * n);
+    AL(V.f, 3 * n);
+    AL(V.type, n);
+    AL(V.id, n);
+    AL(V.bpk, n);
+    AL(V.rec, n);
+    AL(V.recb, n);
+    AL(V.tx, 3 * n);
+    AL(V.tv, 3 * n);
+    AL(V.ttype, n);
+    AL(V.tid, n);
+    AL(V.key, n);
+    AL(V.slot, n);
+    AL(V.perm, n);
+    AL(V.bin_count, (size_t)V.nbins_total);
+    AL(V.bin_start, (size_t)V.nbins_total + 1);
+    AL(V.ncount, n);
+    if (V.pot == MD_POT_EAM_FS) {
+        if (V.prec == MD_PREC_FP64) AL(V.fp64, n);
+        else AL(V.fp32, n);
+        AL(V.emb, n);
+    }
+    AL(V.ev, 8 * n);
+    AL(h->d_tab, 1);
+    AL(h->d_ctl, 1);
+#undef AL
+    V.tab = h->d_tab;
+    V.ctl = h->d_ctl;
+    {
+        md_status st = alloc_list(h, initial_maxneigh(h->reps, rl));
+        if (st) { md_destroy(h); return st; }
+    }
+    std::vector<int> tile_rep(V.n_tiles);
+    for (int r = 0; r < n_rep; ++r)
+        for (int t = 0; t < h->reps[r].ntiles; ++t) tile_rep[h->reps[r].tile0 + t] = r;
+    // validate types on the host (one copy at creation)
+    for (int r = 0; r < n_rep; ++r) {
+        std::vector<int32_t> ht((size_t)cfgs[r].n_atoms);
+        if (cudaMemcpy(ht.data(), type[r], ht.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            md_destroy(h);
+            return fail(nullptr, MD_ERR_CUDA, "cannot read the type array of replica %d", r);
+        }
+        for (int32_t t : ht)
+            if (t < 0 || t >= h->cfg.n_types) {
+                md_destroy(h);
+                return fail(nullptr, MD_ERR_INVALID, "atom type %d out of range in replica %d", t, r);
+            }
+    }
+#define CKD(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            md_status st_ = fail(nullptr, MD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+            md_destroy(h);                                                                 \
+            return st_;                                                                    \
+        }                                                                                  \
+    } while (0)
+    CKD(cudaMemcpyAsync(d_rep, h->reps.data(), sizeof(Rep) * n_rep, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemcpyAsync(d_tile_rep, tile_rep.data(), sizeof(int) * V.n_tiles, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemsetAsync(V.rep_disp, 0, sizeof(unsigned) * n_rep, h->s));
+    CKD(cudaMemsetAsync(V.rep_flag, 0, sizeof(int) * n_rep, h->s));
+    CKD(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->s));
+    CKD(cudaMemsetAsync(V.v, 0, sizeof(double) * 3 * n, h->s));
+    CKD(cudaMemsetAsync(V.f, 0, sizeof(double) * 3 * n, h->s));
+    CKD(cudaMemsetAsync(V.ev, 0, sizeof(double) * 8 * n, h->s));
+    CKD(cudaMemsetAsync(V.ncount, 0, sizeof(int) * n, h->s));
+    CKD(cudaMemsetAsync(V.rec, 0, sizeof(float4) * n, h->s));
+    CKD(cudaMemsetAsync(V.recb, 0, sizeof(float4) * n, h->s));
+    // the caller's arrays are concatenated in replica order: stage each replica
+    for (int r = 0; r < n_rep; ++r) CKD(launch_stage_in(V, r, h->reps[r].natoms, x[r], v[r], type[r], h->s));
+#undef CKD
+    md_status st = upload_tab(h);
+    if (st) { md_destroy(h); return st; }
+    st = full_rebuild(h, true);
+    if (st) { md_destroy(h); return st; }
+    st = compute_forces(h, kModeStoreF);
+    if (st) { md_destroy(h); return st; }
+    if (h->cfg.tpa == 0) {
+        st = md_autotune(h, nullptr);
+        if (st) { md_destroy(h); return st; }
+    }
+    if (cudaStreamSynchronize(h->s) != cudaSuccess) {
+        md_destroy(h);
+        return fail(nullptr, MD_ERR_CUDA, "synchronize after create: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    *out = h;
+    return MD_OK;
+}
+
+// ================================================================ C ABI ==
+
+extern "C" {
+
+md_status md_create(const md_config *cfg, const double *x, const double *v, const int32_t *type,
+                    md_system **out) {
+    if (!cfg) return fail(nullptr, MD_ERR_INVALID, "null config");
+    const double *xs[1] = {x};
+    const double *vs[1] = {v};
+    const int32_t *ts[1] = {type};
+    return create_impl(1, cfg, xs, vs, ts, out);
+}
+
+md_status md_batch_create(int32_t n_rep, const md_config *cfgs, const double *const *x, const double *const *v,
+                          const int32_t *const *type, md_system **out) {
+    if (!cfgs || !x || !v || !type) return fail(nullptr, MD_ERR_INVALID, "null argument");
+    return create_impl(n_rep, cfgs, x, v, type, out);
+}
+
+md_status md_destroy(md_system *h) {
+    if (!h) return MD_OK;
+    cudaStreamSynchronize(h->s);
+    drop_graph(h);
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    delete h;
+    return MD_OK;
+}
+
+md_status md_build_neighbors(md_system *h) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    md_status st = full_rebuild(h, false);
+    if (st) return st;
+    // the sort permutes the atoms: recompute forces in the new order
+    return compute_forces(h, kModeStoreF);
+}
+
+md_status md_compute_forces(md_system *h, double *f_out) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    md_status st = compute_forces(h, kModeStoreF);
+    if (st) return st;
+    if (f_out) CK(h, launch_state_out(h->V, nullptr, nullptr, f_out, h->s));
+    return MD_OK;
+}
+
+md_status md_step(md_system *h, int64_t nsteps) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    if (nsteps < 0) return fail(h, MD_ERR_INVALID, "nsteps < 0");
+    if (nsteps == 0) return MD_OK;
+    if (nsteps > (int64_t)0x7fffffff) return fail(h, MD_ERR_INVALID, "nsteps too large for one call");
+    int rem = (int)nsteps, first = 1;
+    CK(h, cudaMemcpyAsync(&h->d_ctl->remaining, &rem, sizeof(int), cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(&h->d_ctl->first, &first, sizeof(int), cudaMemcpyHostToDevice, h->s));
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        if (!h->exec) {
+            md_status st = build_step_graph(h);
+            if (st) return st;
+        }
+        CK(h, cudaGraphLaunch(h->exec, h->s));
+        Ctl c;
+        md_status st = read_ctl(h, &c);
+        if (st) return st;
+        if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity in md_step");
+        if (c.err & kErrTimeout) return fail(h, MD_ERR_TIMEOUT, "device wait timed out");
+        if (!(c.err & kErrOverflow)) {
+            if (c.remaining != 0) return fail(h, MD_ERR_CUDA, "step loop ended with %d steps left", c.remaining);
+            return MD_OK;
+        }
+        // a rebuild overflowed the list capacity in the middle of a step: the
+        // drift of that step is done and the rebuilt replicas are sorted.
+        // Grow, rebuild their lists, finish the step, continue.
+        st = settle_overflow(h, false);
+        if (st) return st;
+        std::vector<KCall> seq;
+        force_sequence(h->V, kModeStep, h->block, false, seq);
+        CK(h, run_seq(h, seq));
+        st = read_ctl(h, &c);
+        if (st) return st;
+        if (c.remaining <= 0) return MD_OK;
+    }
+    return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: too many overflow recoveries");
+}
+
+md_status md_energy_virial(md_system *h, double *out) {
+    if (!h || !out) return fail(h, MD_ERR_INVALID, "null argument");
+    md_status st = compute_forces(h, kModeEV);
+    if (st) return st;
+    CK(h, launch_ev_reduce(h->V, out, h->s));
+    return MD_OK;
+}
+
+md_status md_get_state(md_system *h, double *x, double *v, double *f) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    CK(h, launch_state_out(h->V, x, v, f, h->s));
+    return MD_OK;
+}
+
+md_status md_set_state(md_system *h, const double *x, const double *v) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    CK(h, launch_restage(h->V, x, v, h->s));
+    md_status st = full_rebuild(h, true);
+    if (st) return st;
+    return compute_forces(h, kModeStoreF);
+}
+
+md_status md_set_params(md_system *h, const double *params) {
+    if (!h || !params) return fail(h, MD_ERR_INVALID, "null argument");
+    if (h->cfg.pot == MD_POT_EAM_FS && params[0] != h->cfg.cutoff)
+        return fail(h, MD_ERR_INVALID, "the EAM cut-off cannot change");
+    if (h->cfg.pot == MD_POT_LJ) {
+        const int nt = h->cfg.n_types;
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nt; ++b)
+                if (params[a * nt + b] != params[b * nt + a] ||
+                    params[nt * nt + a * nt + b] != params[nt * nt + b * nt + a])
+                    return fail(h, MD_ERR_INVALID, "LJ parameters must be symmetric");
+    }
+    h->params.assign(params, params + h->cfg.n_params);
+    md_status st = upload_tab(h);
+    if (st) return st;
+    return compute_forces(h, kModeStoreF);
+}
+
+md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x, double *grad_params) {
+    if (!h || !grad_f) return fail(h, MD_ERR_INVALID, "null argument");
+    if (h->cfg.pot != MD_POT_LJ) return fail(h, MD_ERR_UNSUPPORTED, "backward is implemented for LJ");
+    if (h->V.half) return fail(h, MD_ERR_UNSUPPORTED, "backward needs a full list (md_set_kernel with MD_LIST_FULL)");
+    View &V = h->V;
+    if (!V.gs) {
+        cudaError_t e = dalloc(h, &V.gs, 3 * (size_t)V.n_pad);
+        if (e == cudaSuccess) e = dalloc(h, &V.gx, 3 * (size_t)V.n_pad);
+        if (e != cudaSuccess) return fail(h, MD_ERR_OOM, "backward buffers: %s", cudaGetErrorString(e));
+        drop_graph(h);
+    }
+    const int nb = backward_partial_blocks(V);
+    const int ntm = V.ntypes == 1 ? 1 : (V.ntypes == 2 ? 2 : kMaxTypes);
+    const size_t need = (size_t)nb * 2 * ntm * ntm;
+    if (need > h->gp_part_size) {
+        dfree(h, V.gp_part);
+        V.gp_part = nullptr;
+        cudaError_t e = dalloc(h, &V.gp_part, need);
+        if (e != cudaSuccess) return fail(h, MD_ERR_OOM, "backward partials: %s", cudaGetErrorString(e));
+        h->gp_part_size = need;
+        drop_graph(h);
+    }
+    CK(h, launch_backward(V, grad_f, grad_x, grad_params, nb, h->s));
+    return MD_OK;
+}
+
+md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    if (tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
+        return fail(h, MD_ERR_INVALID, "tpa must be 1,2,4,8,16 or 32");
+    if (list != MD_LIST_FULL && list != MD_LIST_HALF) return fail(h, MD_ERR_INVALID, "list must be FULL or HALF");
+    if (list == MD_LIST_HALF && h->cfg.pot != MD_POT_LJ)
+        return fail(h, MD_ERR_UNSUPPORTED, "half lists are implemented for LJ only");
+    if (block != 64 && block != 128 && block != 256) return fail(h, MD_ERR_INVALID, "block must be 64, 128 or 256");
+    const int half = list == MD_LIST_HALF ? 1 : 0;
+    const bool relayout = (tpa != h->V.tpa) || (half != h->V.half);
+    h->V.tpa = tpa;
+    h->V.half = half;
+    h->block = block;
+    drop_graph(h);
+    if (relayout) return md_build_neighbors(h);
+    return MD_OK;
+}
+
+md_status md_autotune(md_system *h, const char *cache_path) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    Ctl c;
+    md_status st = read_ctl(h, &c);
+    if (st) return st;
+    const double avg = h->n_real > 0 ? (double)c.list_entries / (double)h->n_real : 0.0;
+    char key[256];
+    snprintf(key, sizeof(key), "pot=%d prec=%d n=%lld nrep=%d nbr=%d list=%d", (int)h->cfg.pot, (int)h->cfg.prec,
+             (long long)h->n_real, h->n_rep, (int)std::lround(avg), (int)h->cfg.list);
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        while (std::getline(in, line)) {
+            const size_t bar = line.find('|');
+            if (bar == std::string::npos || line.substr(0, bar) != key) continue;
+            int t = 0, l = 0, b = 0;
+            if (sscanf(line.c_str() + bar + 1, "%d %d %d", &t, &l, &b) == 3)
+                return md_set_kernel(h, t, (md_listkind)l, b);
+        }
+    }
+    std::vector<int> lists;
+    if (h->cfg.list == MD_LIST_FULL || h->cfg.pot != MD_POT_LJ) lists = {MD_LIST_FULL};
+    else if (h->cfg.list == MD_LIST_HALF) lists = {MD_LIST_HALF};
+    else lists = {MD_LIST_FULL, MD_LIST_HALF};
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    double best = 1e300;
+    int bt = 1, bl = MD_LIST_FULL, bb = 256;
+    for (int l : lists)
+        for (int t : {1, 2, 4, 8, 16, 32})
+            for (int b : {128, 256}) {
+                st = md_set_kernel(h, t, (md_listkind)l, b);
+                if (st) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                std::vector<KCall> seq;
+                force_sequence(h->V, kModeStoreF, b, false, seq);
+                for (int w = 0; w < 2; ++w) CK(h, run_seq(h, seq));
+                std::vector<float> ms;
+                for (int rep = 0; rep < 5; ++rep) {
+                    CK(h, cudaEventRecord(e0, h->s));
+                    CK(h, run_seq(h, seq));
+                    CK(h, cudaEventRecord(e1, h->s));
+                    CK(h, cudaEventSynchronize(e1));
+                    float m = 0;
+                    CK(h, cudaEventElapsedTime(&m, e0, e1));
+                    ms.push_back(m);
+                }
+                std::sort(ms.begin(), ms.end());
+                if (ms[2] < best) { best = ms[2]; bt = t; bl = l; bb = b; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st = md_set_kernel(h, bt, (md_listkind)bl, bb);
+    if (st) return st;
+    if (cache_path) {
+        std::ofstream outf(cache_path, std::ios::app);
+        outf << key << "|" << bt << " " << bl << " " << bb << " " << best << "\n";
+    }
+    return MD_OK;
+}
+
+md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_out, double *bytes_out) {
+    if (!h || !ms_out || reps < 1 || warmup < 0) return fail(h, MD_ERR_INVALID, "bad argument");
+    std::vector<KCall> seq;
+    force_sequence(h->V, kModeKickDry, h->block, false, seq);
+    for (int w = 0; w < warmup; ++w) CK(h, run_seq(h, seq));
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    CK(h, cudaEventRecord(e0, h->s));
+    for (int r = 0; r < reps; ++r) CK(h, run_seq(h, seq));
+    CK(h, cudaEventRecord(e1, h->s));
+    CK(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = (double)ms / reps;
+    if (bytes_out) {
+        Ctl c;
+        md_status st = read_ctl(h, &c);
+        if (st) return st;
+        // per atom: record (FP32 16 B or FP64 32 B) + list length 4 B + v in/out 48 B
+        // (+ F'_i 4/8 B and the list a second time for the EAM density pass)
+        const double rec = h->V.prec == MD_PREC_FP64 ? 32.0 : 16.0;
+        double per_atom = rec + 4.0 + 48.0;
+        double list = 4.0 * (double)c.list_entries;
+        if (h->cfg.pot == MD_POT_EAM_FS) {
+            per_atom += rec + 4.0 + 2.0 * (h->V.prec == MD_PREC_FP64 ? 8.0 : 4.0);
+            list *= 2.0;
+        }
+        if (h->V.half) per_atom += 3 * 8.0 * 2 + 24.0;  // F zeroed, atomics' read-modify-write, kick reads F
+        *bytes_out = list + per_atom * (double)h->n_real;
+    }
+    return MD_OK;
+}
+
+md_status md_info(md_system *h, md_info_t *out) {
+    if (!h || !out) return fail(h, MD_ERR_INVALID, "null argument");
+    Ctl c;
+    md_status st = read_ctl(h, &c);
+    if (st) return st;
+    out->n_atoms = h->n_real;
+    out->n_rep = h->n_rep;
+    out->tpa = h->V.tpa;
+    out->list = h->V.half ? MD_LIST_HALF : MD_LIST_FULL;
+    out->block = h->block;
+    out->maxneigh = h->V.maxneigh;
+    out->max_count = c.max_count;
+    out->list_entries = c.list_entries;
+    out->rebuilds = c.rebuilds;
+    out->steps = c.steps;
+    for (int a = 0; a < 3; ++a) out->bins[a] = h->reps[0].nb[a];
+    return MD_OK;
+}
+
+md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t cap) {
+    if (!h || !counts || !nbr) return fail(h, MD_ERR_INVALID, "null argument");
+    Ctl c;
+    md_status st = read_ctl(h, &c);
+    if (st) return st;
+    if (cap < c.max_count) return fail(h, MD_ERR_INVALID, "cap %d < longest list %d", cap, c.max_count);
+    CK(h, launch_neighbors_out(h->V, counts, nbr, cap, h->s));
+    return MD_OK;
+}
+
+md_status md_sync_status(md_system *h) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    CK(h, cudaStreamSynchronize(h->s));
+    CK(h, cudaGetLastError());
+    Ctl c;
+    md_status st = read_ctl(h, &c);
+    if (st) return st;
+    if (c.err) {
+        unsigned zero = 0;
+        CK(h, cudaMemcpyAsync(&h->d_ctl->err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, h->s));
+        CK(h, cudaStreamSynchronize(h->s));
+        if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite state detected on the device");
+        if (c.err & kErrTimeout) return fail(h, MD_ERR_TIMEOUT, "device wait timed out");
+        if (c.err & kErrOverflow) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list overflow");
+    }
+    return MD_OK;
+}
+
+const char *md_last_error(md_system *h) {
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// md_common.cuh -- data layout, kernel parameter block and device helpers
+// shared by the GB300 MD kernels.  Internal to the library.
+//
+// Layout in device memory (one handle = one system or a batch of replicas):
+//   * atoms live in CELL-SORTED order in slots [0, n_pad); each replica owns a
+//     contiguous, 32-aligned range of slots (a whole number of 32-atom tiles),
+//     so a warp's atoms always belong to one replica;
+//   * positions are stored RELATIVE TO THE CENTRE OF THE ATOM'S BIN at the
+//     last build, in FP64 (xr, SoA for the mixed path; pos4 = {x, y, z, type}
+//     for the FP64 path).  Between builds atoms move at most skin/2, so these
+//     stay small and the FP32 copy rec = float(xr) keeps ~1e-7 absolute
+//     accuracy whatever the box size (absolute FP32 coordinates in a 100-sigma
+//     box would only give ~4e-6);
+//   * the neighbour list is a padded array nlist[n_pad * maxneigh] of 32-bit
+//     entries  j | (dx+1) << 26 | (dy+1) << 28 | (dz+1) << 30, where (dx,dy,dz)
+//     is the stencil offset of j's bin relative to i's bin.  The separation
+//     is then d = rec_i - rec_j - (dx hx, dy hy, dz hz), periodic images
+//     included, without any minimum-image arithmetic in the force loop;
+//   * list order is tiled for a thread group of T threads per atom: entry k of
+//     atom i sits at  (i / A) * A * maxneigh + (k / T) * 32 + (i % A) * T + k % T
+//     with A = 32 / T atoms per warp, so every warp-wide list load is one
+//     contiguous 128-byte line (T = 1 is the paper's column-major list).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/md.h"
+
+namespace md {
+
+constexpr int kMaxTypes = MD_MAX_TYPES;
+constexpr int kIdxBits = 26;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+constexpr int kMaxAtoms = 1 << kIdxBits;
+constexpr int kMaxBinsPerAxis = 1023;
+
+// status bits latched in Ctl::err (first error code is also kept in Ctl::code)
+enum : unsigned { kErrOverflow = 1u, kErrNonfinite = 2u, kErrTimeout = 4u };
+
+struct Rep {                // one replica (periodic box), device-resident
+    double L[3];            // box edges
+    double Linv[3];
+    double h[3];            // bin edges, h = L / nb
+    double hinv[3];
+    float hf[3];            // float(h), for the FP32 stencil offsets
+    int nb[3];              // bins per axis (>= 2)
+    int bin0, nbins;        // first global bin, number of bins
+    int atom0, natoms;      // first slot, real atoms
+    int tile0, ntiles;      // first 32-atom tile, tiles
+    long long orig0;        // offset of this replica in the caller's concatenated arrays
+};
+
+struct Ctl {                // device control block of a handle
+    unsigned err;           // latched kErr* bits
+    int remaining;          // steps left in the running md_step
+    int first;              // 1: the next drift applies the half kick from the stored F
+    unsigned ticket_drift;  // last-block tickets (reset by the last block)
+    unsigned ticket_force;
+    unsigned ticket_build;
+    int need_maxneigh;      // largest list length seen by an overflowing build
+    int max_count;          // largest list length at the last build
+    long long list_entries; // entries written at the last build (all rebuilt replicas)
+    long long steps;        // completed time steps
+    long long rebuilds;     // completed replica builds
+};
+
+// Parameters of the potential, per ordered type pair p = ti * nt + tj.
+struct PairTab {
+    // LJ: s(r) = r^-2 (lj1 r^-12 - lj2 r^-6) is -U'(r)/r; U = lj3 r^-12 - lj4 r^-6 - off
+    double lj1[kMaxTypes * kMaxTypes], lj2[kMaxTypes * kMaxTypes];
+    double lj3[kMaxTypes * kMaxTypes], lj4[kMaxTypes * kMaxTypes], off[kMaxTypes * kMaxTypes];
+    double eps[kMaxTypes * kMaxTypes], sig[kMaxTypes * kMaxTypes];
+    float lj1f[kMaxTypes * kMaxTypes], lj2f[kMaxTypes * kMaxTypes];
+    float lj3f[kMaxTypes * kMaxTypes], lj4f[kMaxTypes * kMaxTypes], offf[kMaxTypes * kMaxTypes];
+    double ftm_m[kMaxTypes];  // ftm2v / mass
+    double eam[5];            // rc, A, c0, c1, c2
+    float eamf[5];
+};
+
+// Kernel parameter block, passed BY VALUE to every kernel (and baked into the
+// CUDA graphs; any reallocation rebuilds the graphs).
+struct View {
+    int n_pad, n_tiles, n_rep, nbins_total, maxneigh;
+    int tpa;          // threads per atom the list is laid out for
+    int half;         // 1: half list (each pair once, Newton-3 atomics)
+    int prec;         // md_precision
+    int pot;          // md_potential
+    int ntypes;
+    double dt, rc2, rl2, skin_half2;
+    float rc2f, rl2f_lo, rl2f_hi, skin_half2f;
+    const Rep *rep;
+    const int *tile_rep;
+    unsigned *rep_disp;   // per replica: max |x - x_build|^2 since the build, as float bits
+    int *rep_flag;        // per replica: 1 = rebuild in this step
+    // atom state, sorted order
+    double *xr;           // [3][n_pad] cell-relative positions (mixed)
+    double4_32a *pos4;        // [n_pad] cell-relative positions + type bits (fp64)
+    double *v, *f;        // [3][n_pad]
+    int *type, *id, *bpk; // type, index within the replica, packed bin coordinates
+    float4 *rec, *recb;   // float(xr) + type; the same at the last build
+    // rebuild scratch
+    double *tx, *tv;      // [3][n_pad] staged absolute positions / velocities (old order)
+    int *ttype, *tid, *key, *slot, *perm;
+    int *bin_count, *bin_start;
+    // list
+    uint32_t *nlist;
+    int *ncount;
+    // EAM
+    double *fp64;         // F'(rho) per atom (fp64 path)
+    float *fp32;          // F'(rho) per atom (mixed path)
+    double *emb;          // F(rho) per atom (energy)
+    // per-atom energy / virial for deterministic reductions: [8][n_pad]
+    double *ev;
+    // backward
+    double *gs, *gx;      // [3][n_pad] gradient in / out (sorted)
+    double *gp_part;      // per block partial parameter gradients
+    const PairTab *tab;
+    Ctl *ctl;
+    cudaGraphConditionalHandle cond_loop, cond_rebuild;
+};
+
+// Per-launch arguments (also baked into graph nodes).
+struct KArgs {
+    int mode;       // kernel-specific
+    int all;        // rebuild: 1 = every replica, 0 = replicas flagged by the drift
+    int in_graph;   // 1: the kernel may set graph conditionals
+    int aux;
+};
+
+// force-kernel epilogue modes
+enum : int {
+    kModeStoreF = 0,   // write F
+    kModeStep = 1,     // inside md_step: full kick, or half kick + write F on the last step
+    kModeEV = 2,       // write F and per-atom energy/virial/kinetic terms
+    kModeKickDry = 3   // the in-step memory traffic (v read + written) with a zero kick:
+                       // used to time the force pass without changing the state
+};
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ int unpack_bx(int b) { return b & 1023; }
+__device__ __forceinline__ int unpack_by(int b) { return (b >> 10) & 1023; }
+__device__ __forceinline__ int unpack_bz(int b) { return (b >> 20) & 1023; }
+__device__ __forceinline__ int pack_bins(int bx, int by, int bz) { return bx | (by << 10) | (bz << 20); }
+
+// list slot of entry k of atom p for a T-thread group layout
+__device__ __forceinline__ size_t list_index(int p, int k, int T, int maxn) {
+    const int A = 32 / T;
+    return (size_t)(p / A) * (size_t)(A * maxn) + (size_t)(k / T) * 32 + (size_t)(p % A) * T + (k % T);
+}
+
+// stencil offset component (dx) from an entry field value c = dx + 1 in {0,1,2},
+// as an exact float: magic-number conversion of a small integer
+__device__ __forceinline__ float code_delta(uint32_t e, int shift) {
+    return __int_as_float(0x4B400000u | ((e >> shift) & 3u)) - 12582913.0f;
+}
+
+__device__ __forceinline__ float warp_max(float x) {
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Kahan compensated summation in FP32 (Kahan 1965; error bound
+// (2u + O(n u^2)) sum |y_k| independent of the number of terms, u = 2^-24):
+// c carries the rounding error of every addition back into the next one.
+// Four FP32 additions per term; folded into FP64 once per atom.
+struct KahanF {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float y) {
+        float yc = y - c;
+        float t = s + yc;
+        c = (t - s) - yc;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ void latch_error(Ctl *ctl, unsigned bit) { atomicOr(&ctl->err, bit); }
+
+// last-block-done ticket: returns true in every thread of the last block to
+// arrive (all earlier blocks' global writes are visible to it), false in all
+// other blocks.  Every block must call it exactly once, after its work.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return s_last;
+}
+
+}  // namespace md

@@ -1,0 +1,68 @@
+"""Helpers shared by the GPU parity tests (inputs come from `synth`, expected
+values from `oracle`; nothing here computes the method)."""
+import numpy as np
+
+import oracle
+import synth
+
+TPAS = (1, 2, 4, 8, 16, 32)
+
+# tolerances, relative max-norm max_i |F_i - F_i^ref|_inf / max_i |F_i^ref|_inf
+TOL_FP64 = 1e-12
+TOL_MIXED = 1e-5
+
+
+def rel_maxnorm(a, ref):
+    a = np.asarray(a)
+    ref = np.asarray(ref)
+    return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+
+def wrap_diff(a, b, box):
+    d = np.asarray(a) - np.asarray(b)
+    return d - box * np.round(d / box)
+
+
+def lj_case(cells=10, jitter=0.1, seed=1000, rho=0.8442):
+    """jittered fcc LJ liquid start (sigma = eps = m = 1)"""
+    d = synth.lj_liquid(cells, rho=rho, seed=seed, displacement=jitter)
+    return d
+
+
+def ragged_case(n=777, seed=77, rho=0.8442):
+    """n atoms on a random subset of fcc sites (n not a multiple of 32), jittered"""
+    x, box = synth.fcc_subset(n, rho, seed)
+    x = synth.displace(x, box, 0.05, seed + 1)
+    v = synth.maxwell_boltzmann(n, 1.44, 1.0, seed + 2)
+    return {"x": x, "v": v, "box": box}
+
+
+def gpu_lists(counts, nbr):
+    c = counts.cpu().numpy()
+    nb = nbr.cpu().numpy()
+    return [np.sort(nb[i, :c[i]]) for i in range(c.shape[0])]
+
+
+def assert_lists_equal(got, ref, idx=None):
+    idx = range(len(ref)) if idx is None else idx
+    for k, i in enumerate(idx):
+        g = got[i]
+        assert np.array_equal(g, ref[k]), f"atom {i}: gpu {g.tolist()[:8]}.. ({len(g)}) vs oracle {ref[k].tolist()[:8]}.. ({len(ref[k])})"
+
+
+def half_pairs(counts, nbr):
+    c = counts.cpu().numpy()
+    nb = nbr.cpu().numpy()
+    s = set()
+    for i in range(c.shape[0]):
+        for j in nb[i, :c[i]]:
+            s.add((min(i, int(j)), max(i, int(j))))
+    return s
+
+
+def oracle_pairs(ref):
+    return {(i, int(j)) for i, nb in enumerate(ref) for j in nb if i < j}
+
+
+def margin_ok(x, box, rl, idx=None, margin=1e-9):
+    return oracle.min_gap(x, box, rl, idx) > margin

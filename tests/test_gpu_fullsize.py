@@ -1,0 +1,91 @@
+"""Parity at the benchmark's full sizes, on sampled atoms the oracle computes
+one by one (O(N) each): the 864,000-atom LJ liquid at rc 2.5 and 5.0 (mixed,
+every threads-per-atom layout, plus FP64) and the 500,000-atom EAM metal.
+Inputs are jittered lattices (the perfect lattice has zero net forces, which
+would make a relative force error meaningless)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import TOL_FP64, TOL_MIXED, TPAS, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+SKIN = 0.3
+
+
+def sample(n, m=48, seed=0):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n, m, replace=False))
+    return np.concatenate([[0, n - 1], idx])
+
+
+@pytest.fixture(scope="module", params=[2.5, 5.0])
+def lj864k(request):
+    rc = request.param
+    d = synth.config1(rc=rc, displacement=0.1)
+    x, box = d["x"], d["box"]
+    idx = sample(x.shape[0], 40 if rc == 2.5 else 24, seed=int(rc * 10))
+    assert oracle.min_gap(x, box, rc + SKIN, idx) > 1e-9
+    f, _, _ = oracle.lj_at(x, box, rc, idx)
+    nbr = oracle.neighbors(x, box, rc + SKIN, idx)
+    return dict(d, idx=idx, f=f, nbr=nbr)
+
+
+def test_lj864k_mixed_all_layouts(lj864k):
+    from paper_1009_4330_gb300 import System
+    d = lj864k
+    idx = d["idx"]
+    with System.lj(d["x"], d["v"], d["box"], cutoff=d["rc"], skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
+                   tpa=1) as s:
+        for k, tpa in enumerate(TPAS):
+            for lst in ("full", "half"):
+                s.set_kernel(tpa, lst, 256)
+                f = s.compute_forces().cpu().numpy()
+                assert rel_maxnorm(f[idx], d["f"]) < TOL_MIXED, (tpa, lst)
+                if lst == "full" and k in (0, 5):
+                    counts, nbr = s.neighbors()
+                    c = counts.cpu().numpy()[idx]
+                    nb = nbr[idx].cpu().numpy()
+                    for q in range(len(idx)):
+                        assert np.array_equal(np.sort(nb[q, :c[q]]), d["nbr"][q])
+
+
+def test_lj864k_fp64(lj864k):
+    from paper_1009_4330_gb300 import System
+    d = lj864k
+    with System.lj(d["x"], d["v"], d["box"], cutoff=d["rc"], skin=SKIN, dt=0.005, mass=1.0, precision="fp64",
+                   tpa=8) as s:
+        f = s.compute_forces().cpu().numpy()
+    assert rel_maxnorm(f[d["idx"]], d["f"]) < TOL_FP64
+
+
+def test_lj864k_steps_keep_parity(lj864k):
+    # after the bench's own step loop (with in-graph rebuilds), the forces the
+    # library holds are those of its positions, checked on the sample
+    from paper_1009_4330_gb300 import System
+    d = lj864k
+    if d["rc"] != 2.5:
+        pytest.skip("one cutoff is enough for the stepping check")
+    with System.lj(d["x"], d["v"], d["box"], cutoff=d["rc"], skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
+                   tpa=4) as s:
+        s.step(60)
+        x, _, f = (a.cpu().numpy() for a in s.state())
+        assert s.info()["rebuilds"] >= 2
+    idx = d["idx"]
+    fr, _, _ = oracle.lj_at(x, d["box"], d["rc"], idx)
+    assert rel_maxnorm(f[idx], fr) < TOL_MIXED
+
+
+def test_eam500k_mixed_and_fp64():
+    from paper_1009_4330_gb300 import System
+    d = synth.config2(displacement=0.1)
+    x, box = d["x"], d["box"]
+    idx = sample(x.shape[0], 12, seed=3)
+    fr, rho = oracle.eam_at(x, box, d["eam"], idx)
+    for prec, tol in (("mixed", TOL_MIXED), ("fp64", TOL_FP64)):
+        with System.eam(x, d["v"], box, eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
+                        ftm2v=d["ftm2v"], precision=prec, tpa=4) as s:
+            f = s.compute_forces().cpu().numpy()
+        assert rel_maxnorm(f[idx], fr) < tol, prec
