@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--cells", type=int, default=60)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / rc 5.0 / EAM / batch side runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--tpa", type=int, default=0, help="threads per atom (0: set-up mini-benchmark picks)")
+    ap.add_argument("--list", default="auto", choices=["auto", "full", "half"])
+    ap.add_argument("--vec", type=int, default=0, help="list entries per thread per load (0: default for tpa)")
+    ap.add_argument("--eager", action="store_true",
+                    help="step without CUDA graphs (kernels launched one by one; for profilers)")
     return ap.parse_args()
 
 
@@ -133,17 +138,17 @@ class ClockSampler:
 
 # ------------------------------------------------------------- workloads --
 
-def make_lj(synth, cells, rc, prec, tpa=0):
+def make_lj(synth, cells, rc, prec, tpa=0, lst="auto"):
     from paper_1009_4330_gb300 import System
     d = synth.config1(rc=rc, cells=cells)
     s = System.lj(d["x"], d["v"], d["box"], cutoff=rc, skin=d["skin"], dt=d["dt"], mass=1.0, precision=prec,
-                  list="auto", tpa=tpa)
+                  list=lst, tpa=tpa)
     return s, d
 
 
-def time_steps(s, K, W, sampler_gpu=None):
+def time_steps(s, K, W, sampler_gpu=None, eager=False):
     import torch
-    s.step(W)
+    s.step(W, eager=eager)
     torch.cuda.synchronize()
     i0 = s.info()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -153,7 +158,7 @@ def time_steps(s, K, W, sampler_gpu=None):
         clocks.__enter__()
     torch.cuda.synchronize()
     e0.record()
-    s.step(K)
+    s.step(K, eager=eager)
     e1.record()
     torch.cuda.synchronize()
     if clocks:
@@ -268,11 +273,14 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dist = dist_init(ws)
     cells = args.cells
-    s, d = make_lj(synth, cells, 2.5, "mixed", tpa=0)  # tpa 0: set-up mini-benchmark picks the layout
+    # tpa 0: the set-up mini-benchmark picks threads per atom, list kind and block size
+    s, d = make_lj(synth, cells, 2.5, "mixed", tpa=args.tpa, lst=args.list if args.tpa else "auto")
+    if args.tpa and args.vec:
+        s.set_kernel(args.tpa, args.list if args.list != "auto" else "full", 256, args.vec)
     n = d["x"].shape[0]
     K, W = args.steps, max(3, args.warmup)
     barrier(dist)
-    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local)
+    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local, eager=args.eager)
     ms = max_over_ranks(dist, ms)
     value = ws * n * K / (ms / 1000.0)
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
@@ -297,6 +305,7 @@ def run_ours(args, ws, rank, local):
             "dtype": "f32 pair math, f64 accumulate/integrate", "data": "synthetic",
             "config": {"workload": WORKLOAD, "atoms": n, "cells": cells, "rc": 2.5, "skin": 0.3, "dt": 0.005,
                        "precision": "mixed", "tpa": info["tpa"], "list": info["list"], "block": info["block"],
+                       "vec": info["vec"], "graph": not args.eager,
                        "avg_list_length": info["list_entries"] / n, "rebuilds_in_timed_region": rebuilds,
                        "steps_per_rebuild": (K / rebuilds) if rebuilds else None,
                        "l2": "working set > L2 (list alone ~0.3 GB): no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},

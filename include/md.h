@@ -181,8 +181,24 @@ md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x,
  */
 md_status md_autotune(md_system *h, const char *cache_path);
 
-/* Select the force-kernel variant directly: tpa in {1,2,4,8,16,32}, list FULL or HALF, block 64..1024. */
-md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block);
+/*
+ * Select the force-kernel variant directly: tpa (threads per atom) in
+ * {1,2,4,8,16,32}, list FULL or HALF, block (threads per block) in
+ * {64,128,256}, vec (list entries per thread per load) in {1,4}.  Changing
+ * tpa, list or vec rebuilds the list in the matching layout (and recomputes
+ * the forces).
+ */
+md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block, int32_t vec);
+
+/*
+ * md_step without CUDA graphs: the step's kernels are launched one by one
+ * and the list-rebuild kernels every step (each returns at once for replicas
+ * whose displacement check did not ask for a rebuild).  Same results as
+ * md_step; slower per step.  For profilers that cannot follow kernels inside
+ * conditional graph nodes, and for environments without them.  An overflow
+ * of the list capacity is reported (MD_ERR_LIST_OVERFLOW), not recovered.
+ */
+md_status md_step_eager(md_system *h, int64_t nsteps);
 
 typedef struct {
     int64_t n_atoms;         /* total real atoms                                          */
@@ -191,6 +207,7 @@ typedef struct {
     int32_t list;            /* current md_listkind (FULL or HALF)                        */
     int32_t block;           /* threads per block of the force kernel                     */
     int32_t maxneigh;        /* list capacity per atom                                    */
+    int32_t vec;             /* list entries per thread per load                          */
     int32_t max_count;       /* largest list length at the last build                     */
     int64_t list_entries;    /* total list entries at the last build                      */
     int64_t rebuilds;        /* list builds since creation                                */

@@ -19,7 +19,7 @@ MD_MAX_TYPES = 8
 EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "md_compute_forces", "md_step",
            "md_energy_virial", "md_get_state", "md_set_state", "md_set_params", "md_forces_backward",
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
-           "md_time_force")
+           "md_time_force", "md_step_eager")
 
 
 class MdConfig(ctypes.Structure):
@@ -34,7 +34,7 @@ class MdConfig(ctypes.Structure):
 class MdInfo(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("n_rep", ctypes.c_int32), ("tpa", ctypes.c_int32),
                 ("list", ctypes.c_int32), ("block", ctypes.c_int32), ("maxneigh", ctypes.c_int32),
-                ("max_count", ctypes.c_int32), ("list_entries", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
+                ("vec", ctypes.c_int32), ("max_count", ctypes.c_int32), ("list_entries", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("bins", ctypes.c_int32 * 3)]
 
 
@@ -70,7 +70,8 @@ def load(build_if_missing: bool = True):
         "md_set_params": [vp, P(d)],
         "md_forces_backward": [vp, vp, vp, vp],
         "md_autotune": [vp, ctypes.c_char_p],
-        "md_set_kernel": [vp, i32, ctypes.c_int, i32],
+        "md_set_kernel": [vp, i32, ctypes.c_int, i32, i32],
+        "md_step_eager": [vp, i64],
         "md_info": [vp, P(MdInfo)],
         "md_get_neighbors": [vp, vp, vp, i32],
         "md_sync_status": [vp],

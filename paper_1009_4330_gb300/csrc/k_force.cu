@@ -70,11 +70,75 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
     return v;
 }
 
+__device__ __forceinline__ uint4 ld_stream4(const uint32_t *p) {
+    uint4 v;
+    asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // reduce a double over the T consecutive lanes of a group
 template <int T>
 __device__ __forceinline__ double group_sum(double x) {
     for (int o = T / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
+}
+
+// Walk this thread's share of atom i's list: rounds of T*Q entries, the
+// thread's Q entries arriving in one (vector) load, the next round's load
+// issued before this round's work; the Q records are gathered before any
+// arithmetic so that Q gathers are in flight.  For each entry calls
+// pair(e, dx, dy, dz, r2, tj) with d = x_i - x_j (periodic image included).
+template <int PREC, int T, int Q, class Pair>
+__device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int sub, int cnt,
+                                          typename Pol<PREC>::real xi, typename Pol<PREC>::real yi,
+                                          typename Pol<PREC>::real zi, typename Pol<PREC>::real hx,
+                                          typename Pol<PREC>::real hy, typename Pol<PREC>::real hz, Pair &pair) {
+    using P = Pol<PREC>;
+    using real = typename P::real;
+    constexpr int PER = T * Q;
+    const int nr = (cnt + PER - 1) / PER;
+    uint32_t cur[Q], nxt[Q];
+    if (nr > 0) {
+        if (Q == 4) {
+            const uint4 u = ld_stream4(lp);
+            cur[0] = u.x; cur[Q > 1 ? 1 : 0] = u.y; cur[Q > 2 ? 2 : 0] = u.z; cur[Q > 3 ? 3 : 0] = u.w;
+        } else {
+            cur[0] = ld_stream(lp);
+        }
+    }
+    for (int r = 0; r < nr; ++r) {
+        if (r + 1 < nr) {
+            const uint32_t *np = lp + (size_t)(r + 1) * 32 * Q;
+            if (Q == 4) {
+                const uint4 u = ld_stream4(np);
+                nxt[0] = u.x; nxt[Q > 1 ? 1 : 0] = u.y; nxt[Q > 2 ? 2 : 0] = u.z; nxt[Q > 3 ? 3 : 0] = u.w;
+            } else {
+                nxt[0] = ld_stream(np);
+            }
+        }
+        const int left = cnt - (r * PER + sub * Q);
+        real xj[Q], yj[Q], zj[Q];
+        int tj[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q < left) P::load(V, (int)(cur[q] & kIdxMask), xj[q], yj[q], zj[q], tj[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q < left) {
+                const uint32_t e = cur[q];
+                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj[q]);
+                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj[q]);
+                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj[q]);
+                const real r2 = dx * dx + dy * dy + dz * dz;
+                pair(e, dx, dy, dz, r2, tj[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
+    }
 }
 
 // Epilogue of atom p (after the group reduction), by the group's lane 0.
@@ -124,7 +188,41 @@ __device__ __forceinline__ void finish_step(const View &V, const KArgs &a) {
 // FULL: every neighbour in i's list, F_i only, no atomics.
 // HALF: each pair once; F_j -= f_ij by FP64 atomics, F_i += sum by one atomic
 //       per component at the end (F zeroed beforehand; kick in k_kick).
-template <int PREC, int T, int HALF, int EV, int MT>
+template <int PREC, int MT, int HALF, int EV>
+struct LJPair {
+    using real = typename Pol<PREC>::real;
+    using Acc = typename Pol<PREC>::Acc;
+    const View *V;
+    const real *lj1, *lj2, *lj3, *lj4, *off;
+    real rc2;
+    int ti, nt, n;
+    Acc ax, ay, az, e;
+    Acc w[6];
+    __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int tj) {
+        if (r2 < rc2) {
+            const int tp = MT ? ti * nt + tj : 0;
+            const real r2i = Pol<PREC>::rcp(r2);
+            const real r6i = r2i * r2i * r2i;
+            const real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
+            const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
+            ax.add(fxp); ay.add(fyp); az.add(fzp);
+            if (HALF) {
+                const int j = (int)(ent & kIdxMask);
+                atomicAdd(&V->f[j], -(double)fxp);
+                atomicAdd(&V->f[n + j], -(double)fyp);
+                atomicAdd(&V->f[2 * n + j], -(double)fzp);
+            }
+            if (EV) {
+                const real wgt = HALF ? (real)1 : (real)0.5;
+                e.add(wgt * (r6i * (lj3[tp] * r6i - lj4[tp]) - off[tp]));
+                w[0].add(wgt * dx * fxp); w[1].add(wgt * dy * fyp); w[2].add(wgt * dz * fzp);
+                w[3].add(wgt * dx * fyp); w[4].add(wgt * dx * fzp); w[5].add(wgt * dy * fzp);
+            }
+        }
+    }
+};
+
+template <int PREC, int T, int Q, int HALF, int EV, int MT>
 __global__ void __launch_bounds__(256) k_lj(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
@@ -153,65 +251,34 @@ __global__ void __launch_bounds__(256) k_lj(View V, KArgs a) {
     const int sub = lane & (T - 1);
     const bool warp_in = (gw * A < V.n_pad) && err == 0;
 
-    typename P::Acc ax, ay, az;
-    ax.zero(); ay.zero(); az.zero();
-    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
+    LJPair<PREC, MT, HALF, EV> pr;
+    pr.V = &V;
+    pr.lj1 = s_lj1; pr.lj2 = s_lj2; pr.lj3 = s_lj3; pr.lj4 = s_lj4; pr.off = s_off;
+    pr.rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
+    pr.nt = V.ntypes;
+    pr.n = V.n_pad;
+    pr.ti = 0;
+    pr.ax.zero(); pr.ay.zero(); pr.az.zero(); pr.e.zero();
+    for (int k = 0; k < 6; ++k) pr.w[k].zero();
     bool valid = false;
-    int ti = 0;
     if (warp_in) {
         const Rep &R = V.rep[V.tile_rep[p >> 5]];
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
             const int cnt = V.ncount[p];
             real xi, yi, zi;
-            P::load(V, p, xi, yi, zi, ti);
-            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
-            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
-            const int maxn = V.maxneigh;
-            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
-            const int n = V.n_pad;
-            for (int k = sub; k < cnt; k += T, lp += 32) {
-                const uint32_t e = ld_stream(lp);
-                const int j = (int)(e & kIdxMask);
-                real xj, yj, zj;
-                int tj;
-                P::load(V, j, xj, yj, zj, tj);
-                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
-                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
-                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
-                const real r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2) {
-                    const int tp = MT ? ti * V.ntypes + tj : 0;
-                    const real r2i = P::rcp(r2);
-                    const real r6i = r2i * r2i * r2i;
-                    const real fpair = r6i * (s_lj1[tp] * r6i - s_lj2[tp]) * r2i;
-                    const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
-                    ax.add(fxp); ay.add(fyp); az.add(fzp);
-                    if (HALF) {
-                        atomicAdd(&V.f[j], -(double)fxp);
-                        atomicAdd(&V.f[n + j], -(double)fyp);
-                        atomicAdd(&V.f[2 * n + j], -(double)fzp);
-                    }
-                    if (EV) {
-                        const double wgt = HALF ? 1.0 : 0.5;
-                        e_acc += wgt * (double)(r6i * (s_lj3[tp] * r6i - s_lj4[tp]) - s_off[tp]);
-                        w_acc[0] += wgt * (double)(dx * fxp);
-                        w_acc[1] += wgt * (double)(dy * fyp);
-                        w_acc[2] += wgt * (double)(dz * fzp);
-                        w_acc[3] += wgt * (double)(dx * fyp);
-                        w_acc[4] += wgt * (double)(dx * fzp);
-                        w_acc[5] += wgt * (double)(dy * fzp);
-                    }
-                }
-            }
+            P::load(V, p, xi, yi, zi, pr.ti);
+            const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
+            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
         }
     }
-    double fx = group_sum<T>(ax.value());
-    double fy = group_sum<T>(ay.value());
-    double fz = group_sum<T>(az.value());
+    const double fx = group_sum<T>(pr.ax.value());
+    const double fy = group_sum<T>(pr.ay.value());
+    const double fz = group_sum<T>(pr.az.value());
+    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
     if (EV) {
-        e_acc = group_sum<T>(e_acc);
-        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(w_acc[k]);
+        e_acc = group_sum<T>(pr.e.value());
+        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(pr.w[k].value());
     }
     if (valid && sub == 0) {
         if (HALF) {
@@ -224,8 +291,8 @@ __global__ void __launch_bounds__(256) k_lj(View V, KArgs a) {
                 for (int k = 0; k < 6; ++k) V.ev[(2 + k) * n + p] = w_acc[k];
             }
         } else {
-            epilogue(V, a.mode, rem, p, ti, fx, fy, fz, s_ftm);
-            if (EV) write_ev(V, p, ti, e_acc, w_acc, s_ftm);
+            epilogue(V, a.mode, rem, p, pr.ti, fx, fy, fz, s_ftm);
+            if (EV) write_ev(V, p, pr.ti, e_acc, w_acc, s_ftm);
         }
     }
     if (!HALF) finish_step(V, a);
@@ -272,7 +339,21 @@ __global__ void k_kick(View V, KArgs a) {
 
 // pass 1: host density rho_i = sum_j (rc - r)^2 and the embedding derivative
 // F'(rho_i) = -A / (2 sqrt(rho_i)) (0 at rho = 0), FP64 per atom
-template <int PREC, int T>
+template <int PREC>
+struct RhoPair {
+    using real = typename Pol<PREC>::real;
+    typename Pol<PREC>::Acc acc;
+    real rc, rc2;
+    __device__ __forceinline__ void operator()(uint32_t, real, real, real, real r2, int) {
+        if (r2 < rc2) {
+            const real r = r2 * Pol<PREC>::rsqrt(r2);
+            const real t = rc - r;
+            acc.add(t * t);
+        }
+    }
+};
+
+template <int PREC, int T, int Q>
 __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
@@ -282,8 +363,10 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int p = gw * A + lane / T;
     const int sub = lane & (T - 1);
-    typename P::Acc acc;
-    acc.zero();
+    RhoPair<PREC> pr;
+    pr.acc.zero();
+    pr.rc = (PREC == MD_PREC_FP64) ? (real)V.tab->eam[0] : (real)V.tab->eamf[0];
+    pr.rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
     bool valid = false;
     if (gw * A < V.n_pad && err == 0) {
         const Rep &R = V.rep[V.tile_rep[p >> 5]];
@@ -293,30 +376,11 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
             real xi, yi, zi;
             int ti;
             P::load(V, p, xi, yi, zi, ti);
-            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
-            const real rc = (PREC == MD_PREC_FP64) ? (real)V.tab->eam[0] : (real)V.tab->eamf[0];
-            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
-            const int maxn = V.maxneigh;
-            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
-            for (int k = sub; k < cnt; k += T, lp += 32) {
-                const uint32_t e = ld_stream(lp);
-                const int j = (int)(e & kIdxMask);
-                real xj, yj, zj;
-                int tj;
-                P::load(V, j, xj, yj, zj, tj);
-                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
-                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
-                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
-                const real r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2) {
-                    const real r = r2 * P::rsqrt(r2);
-                    const real t = rc - r;
-                    acc.add(t * t);
-                }
-            }
+            const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
+            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
         }
     }
-    const double rho = group_sum<T>(acc.value());
+    const double rho = group_sum<T>(pr.acc.value());
     if (valid && sub == 0) {
         const double Aemb = V.tab->eam[1];
         const double sr = sqrt(rho);
@@ -328,7 +392,36 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
 }
 
 // pass 2: F_i = -sum_j [phi'(r) + (F'_i + F'_j) rho'(r)] d / r
-template <int PREC, int T, int EV>
+template <int PREC, int EV>
+struct EamPair {
+    using real = typename Pol<PREC>::real;
+    using Acc = typename Pol<PREC>::Acc;
+    const View *V;
+    real rc, rc2, c0, c1, c2, fpi;
+    Acc ax, ay, az, e;
+    Acc w[6];
+    __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int) {
+        if (r2 < rc2) {
+            const real fpj = Pol<PREC>::fp(*V, (int)(ent & kIdxMask));
+            const real rinv = Pol<PREC>::rsqrt(r2);
+            const real r = r2 * rinv;
+            const real t = rc - r;
+            const real poly = c0 + r * (c1 + r * c2);
+            const real dpoly = c1 + (real)2 * c2 * r;
+            // -(phi' + (F'_i + F'_j) rho') / r with phi' = -2t poly + t^2 dpoly, rho' = -2t
+            const real coef = -t * ((real)-2 * poly + t * dpoly - (real)2 * (fpi + fpj)) * rinv;
+            const real fxp = dx * coef, fyp = dy * coef, fzp = dz * coef;
+            ax.add(fxp); ay.add(fyp); az.add(fzp);
+            if (EV) {
+                e.add((real)0.5 * t * t * poly);
+                w[0].add((real)0.5 * dx * fxp); w[1].add((real)0.5 * dy * fyp); w[2].add((real)0.5 * dz * fzp);
+                w[3].add((real)0.5 * dx * fyp); w[4].add((real)0.5 * dx * fzp); w[5].add((real)0.5 * dy * fzp);
+            }
+        }
+    }
+};
+
+template <int PREC, int T, int Q, int EV>
 __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
@@ -342,9 +435,17 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int p = gw * A + lane / T;
     const int sub = lane & (T - 1);
-    typename P::Acc ax, ay, az;
-    ax.zero(); ay.zero(); az.zero();
-    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
+    EamPair<PREC, EV> pr;
+    pr.V = &V;
+    if (PREC == MD_PREC_FP64) {
+        pr.rc = V.tab->eam[0]; pr.c0 = V.tab->eam[2]; pr.c1 = V.tab->eam[3]; pr.c2 = V.tab->eam[4];
+    } else {
+        pr.rc = V.tab->eamf[0]; pr.c0 = V.tab->eamf[2]; pr.c1 = V.tab->eamf[3]; pr.c2 = V.tab->eamf[4];
+    }
+    pr.rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
+    pr.fpi = 0;
+    pr.ax.zero(); pr.ay.zero(); pr.az.zero(); pr.e.zero();
+    for (int k = 0; k < 6; ++k) pr.w[k].zero();
     bool valid = false;
     int ti = 0;
     if (gw * A < V.n_pad && err == 0) {
@@ -354,56 +455,18 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
             const int cnt = V.ncount[p];
             real xi, yi, zi;
             P::load(V, p, xi, yi, zi, ti);
-            const real hx = P::h(R, 0), hy = P::h(R, 1), hz = P::h(R, 2);
-            real rc, c0, c1, c2;
-            if (PREC == MD_PREC_FP64) {
-                rc = V.tab->eam[0]; c0 = V.tab->eam[2]; c1 = V.tab->eam[3]; c2 = V.tab->eam[4];
-            } else {
-                rc = V.tab->eamf[0]; c0 = V.tab->eamf[2]; c1 = V.tab->eamf[3]; c2 = V.tab->eamf[4];
-            }
-            const real rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
-            const real fpi = P::fp(V, p);
-            const int maxn = V.maxneigh;
-            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
-            for (int k = sub; k < cnt; k += T, lp += 32) {
-                const uint32_t e = ld_stream(lp);
-                const int j = (int)(e & kIdxMask);
-                real xj, yj, zj;
-                int tj;
-                P::load(V, j, xj, yj, zj, tj);
-                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj);
-                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj);
-                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj);
-                const real r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2) {
-                    const real rinv = P::rsqrt(r2);
-                    const real r = r2 * rinv;
-                    const real t = rc - r;
-                    const real poly = c0 + r * (c1 + r * c2);
-                    const real dpoly = c1 + (real)2 * c2 * r;
-                    // -(phi' + (F'_i + F'_j) rho') / r with phi' = -2t poly + t^2 dpoly, rho' = -2t
-                    const real coef = -t * ((real)-2 * poly + t * dpoly - (real)2 * (fpi + P::fp(V, j))) * rinv;
-                    const real fxp = dx * coef, fyp = dy * coef, fzp = dz * coef;
-                    ax.add(fxp); ay.add(fyp); az.add(fzp);
-                    if (EV) {
-                        e_acc += 0.5 * (double)(t * t * poly);
-                        w_acc[0] += 0.5 * (double)(dx * fxp);
-                        w_acc[1] += 0.5 * (double)(dy * fyp);
-                        w_acc[2] += 0.5 * (double)(dz * fzp);
-                        w_acc[3] += 0.5 * (double)(dx * fyp);
-                        w_acc[4] += 0.5 * (double)(dx * fzp);
-                        w_acc[5] += 0.5 * (double)(dy * fzp);
-                    }
-                }
-            }
+            pr.fpi = P::fp(V, p);
+            const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
+            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
         }
     }
-    const double fx = group_sum<T>(ax.value());
-    const double fy = group_sum<T>(ay.value());
-    const double fz = group_sum<T>(az.value());
+    const double fx = group_sum<T>(pr.ax.value());
+    const double fy = group_sum<T>(pr.ay.value());
+    const double fz = group_sum<T>(pr.az.value());
+    double e_acc = 0.0, w_acc[6] = {0, 0, 0, 0, 0, 0};
     if (EV) {
-        e_acc = group_sum<T>(e_acc);
-        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(w_acc[k]);
+        e_acc = group_sum<T>(pr.e.value());
+        for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(pr.w[k].value());
     }
     if (valid && sub == 0) {
         epilogue(V, a.mode, rem, p, ti, fx, fy, fz, s_ftm);
@@ -514,50 +577,66 @@ __global__ void k_loop_init(View V, KArgs a) {
 
 // ------------------------------------------------------------- dispatch ----
 
-template <int PREC, int HALF, int EV, int MT>
-static const void *pick_lj(int T) {
+template <int PREC, int Q, int HALF, int EV, int MT>
+static const void *pick_lj_t(int T) {
     switch (T) {
-        case 1: return (const void *)k_lj<PREC, 1, HALF, EV, MT>;
-        case 2: return (const void *)k_lj<PREC, 2, HALF, EV, MT>;
-        case 4: return (const void *)k_lj<PREC, 4, HALF, EV, MT>;
-        case 8: return (const void *)k_lj<PREC, 8, HALF, EV, MT>;
-        case 16: return (const void *)k_lj<PREC, 16, HALF, EV, MT>;
-        default: return (const void *)k_lj<PREC, 32, HALF, EV, MT>;
+        case 1: return (const void *)k_lj<PREC, 1, Q, HALF, EV, MT>;
+        case 2: return (const void *)k_lj<PREC, 2, Q, HALF, EV, MT>;
+        case 4: return (const void *)k_lj<PREC, 4, Q, HALF, EV, MT>;
+        case 8: return (const void *)k_lj<PREC, 8, Q, HALF, EV, MT>;
+        case 16: return (const void *)k_lj<PREC, 16, Q, HALF, EV, MT>;
+        default: return (const void *)k_lj<PREC, 32, Q, HALF, EV, MT>;
     }
 }
 
-template <int PREC>
-static const void *pick_lj_prec(int T, int half, int ev, int mt) {
+template <int PREC, int Q>
+static const void *pick_lj_q(int T, int half, int ev, int mt) {
     if (half) {
-        if (ev) return mt ? pick_lj<PREC, 1, 1, 1>(T) : pick_lj<PREC, 1, 1, 0>(T);
-        return mt ? pick_lj<PREC, 1, 0, 1>(T) : pick_lj<PREC, 1, 0, 0>(T);
+        if (ev) return mt ? pick_lj_t<PREC, Q, 1, 1, 1>(T) : pick_lj_t<PREC, Q, 1, 1, 0>(T);
+        return mt ? pick_lj_t<PREC, Q, 1, 0, 1>(T) : pick_lj_t<PREC, Q, 1, 0, 0>(T);
     }
-    if (ev) return mt ? pick_lj<PREC, 0, 1, 1>(T) : pick_lj<PREC, 0, 1, 0>(T);
-    return mt ? pick_lj<PREC, 0, 0, 1>(T) : pick_lj<PREC, 0, 0, 0>(T);
+    if (ev) return mt ? pick_lj_t<PREC, Q, 0, 1, 1>(T) : pick_lj_t<PREC, Q, 0, 1, 0>(T);
+    return mt ? pick_lj_t<PREC, Q, 0, 0, 1>(T) : pick_lj_t<PREC, Q, 0, 0, 0>(T);
 }
 
 template <int PREC>
-static const void *pick_rho(int T) {
+static const void *pick_lj_prec(int T, int Q, int half, int ev, int mt) {
+    return Q == 4 ? pick_lj_q<PREC, 4>(T, half, ev, mt) : pick_lj_q<PREC, 1>(T, half, ev, mt);
+}
+
+template <int PREC, int Q>
+static const void *pick_rho_q(int T) {
     switch (T) {
-        case 1: return (const void *)k_eam_rho<PREC, 1>;
-        case 2: return (const void *)k_eam_rho<PREC, 2>;
-        case 4: return (const void *)k_eam_rho<PREC, 4>;
-        case 8: return (const void *)k_eam_rho<PREC, 8>;
-        case 16: return (const void *)k_eam_rho<PREC, 16>;
-        default: return (const void *)k_eam_rho<PREC, 32>;
+        case 1: return (const void *)k_eam_rho<PREC, 1, Q>;
+        case 2: return (const void *)k_eam_rho<PREC, 2, Q>;
+        case 4: return (const void *)k_eam_rho<PREC, 4, Q>;
+        case 8: return (const void *)k_eam_rho<PREC, 8, Q>;
+        case 16: return (const void *)k_eam_rho<PREC, 16, Q>;
+        default: return (const void *)k_eam_rho<PREC, 32, Q>;
     }
 }
 
-template <int PREC, int EV>
-static const void *pick_eamf(int T) {
+template <int PREC>
+static const void *pick_rho(int T, int Q) {
+    return Q == 4 ? pick_rho_q<PREC, 4>(T) : pick_rho_q<PREC, 1>(T);
+}
+
+template <int PREC, int Q, int EV>
+static const void *pick_eamf_q(int T) {
     switch (T) {
-        case 1: return (const void *)k_eam_force<PREC, 1, EV>;
-        case 2: return (const void *)k_eam_force<PREC, 2, EV>;
-        case 4: return (const void *)k_eam_force<PREC, 4, EV>;
-        case 8: return (const void *)k_eam_force<PREC, 8, EV>;
-        case 16: return (const void *)k_eam_force<PREC, 16, EV>;
-        default: return (const void *)k_eam_force<PREC, 32, EV>;
+        case 1: return (const void *)k_eam_force<PREC, 1, Q, EV>;
+        case 2: return (const void *)k_eam_force<PREC, 2, Q, EV>;
+        case 4: return (const void *)k_eam_force<PREC, 4, Q, EV>;
+        case 8: return (const void *)k_eam_force<PREC, 8, Q, EV>;
+        case 16: return (const void *)k_eam_force<PREC, 16, Q, EV>;
+        default: return (const void *)k_eam_force<PREC, 32, Q, EV>;
     }
+}
+
+template <int PREC>
+static const void *pick_eamf(int T, int Q, int ev) {
+    if (Q == 4) return ev ? pick_eamf_q<PREC, 4, 1>(T) : pick_eamf_q<PREC, 4, 0>(T);
+    return ev ? pick_eamf_q<PREC, 1, 1>(T) : pick_eamf_q<PREC, 1, 0>(T);
 }
 
 void force_sequence(const View &V, int mode, int block, bool in_graph, std::vector<KCall> &seq) {
@@ -571,8 +650,8 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
     const int fp64 = (V.prec == MD_PREC_FP64);
     if (V.pot == MD_POT_LJ) {
         const int mt = V.ntypes > 1 ? 1 : 0;
-        const void *fn = fp64 ? pick_lj_prec<MD_PREC_FP64>(T, V.half, ev, mt)
-                              : pick_lj_prec<MD_PREC_MIXED>(T, V.half, ev, mt);
+        const void *fn = fp64 ? pick_lj_prec<MD_PREC_FP64>(T, V.vec, V.half, ev, mt)
+                              : pick_lj_prec<MD_PREC_MIXED>(T, V.vec, V.half, ev, mt);
         if (V.half) {
             seq.push_back(KCall{(const void *)k_zero_f, dim3((3 * V.n_pad + 255) / 256), dim3(256), 0, a});
             KArgs af = a;
@@ -586,9 +665,9 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
     } else {
         KArgs ar = a;
         ar.in_graph = 0;
-        seq.push_back(KCall{fp64 ? pick_rho<MD_PREC_FP64>(T) : pick_rho<MD_PREC_MIXED>(T), grid, dim3(block), 0, ar});
-        const void *fn = fp64 ? (ev ? pick_eamf<MD_PREC_FP64, 1>(T) : pick_eamf<MD_PREC_FP64, 0>(T))
-                              : (ev ? pick_eamf<MD_PREC_MIXED, 1>(T) : pick_eamf<MD_PREC_MIXED, 0>(T));
+        seq.push_back(KCall{fp64 ? pick_rho<MD_PREC_FP64>(T, V.vec) : pick_rho<MD_PREC_MIXED>(T, V.vec), grid,
+                            dim3(block), 0, ar});
+        const void *fn = fp64 ? pick_eamf<MD_PREC_FP64>(T, V.vec, ev) : pick_eamf<MD_PREC_MIXED>(T, V.vec, ev);
         seq.push_back(KCall{fn, grid, dim3(block), 0, a});
     }
 }

@@ -85,22 +85,32 @@ __global__ void k_state_out(View V, double *x, double *v, double *f) {
 
 // ------------------------------------------------------ energy / virial ----
 
-// out[8 r + k] = sum over replica r's atoms of ev[k][p], fixed order
+// Two fixed-order stages: per 32-atom tile (one warp each), then per
+// replica over its tiles in order (one block each).
+__global__ void k_ev_tiles(View V) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= V.n_tiles) return;
+    const int p = t * 32 + lane;
+    const Rep &R = V.rep[V.tile_rep[t]];
+    const bool ok = (p - R.atom0) < R.natoms;
+    for (int k = 0; k < 8; ++k) {
+        double x = ok ? V.ev[k * V.n_pad + p] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) V.ev_tile[(size_t)t * 8 + k] = x;
+    }
+}
+
 __global__ void k_ev_reduce(View V, double *out) {
-    __shared__ double s[8][256];
+    __shared__ double s_w[32];
     const int r = blockIdx.x;
     const Rep &R = V.rep[r];
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int p = R.atom0 + threadIdx.x; p < R.atom0 + R.natoms; p += blockDim.x)
-        for (int k = 0; k < 8; ++k) acc[k] += V.ev[k * V.n_pad + p];
-    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int k = 0; k < 8; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
-        __syncthreads();
+    for (int k = 0; k < 8; ++k) {
+        double acc = 0.0;
+        for (int t = R.tile0 + threadIdx.x; t < R.tile0 + R.ntiles; t += blockDim.x) acc += V.ev_tile[(size_t)t * 8 + k];
+        const double tot = block_sum(acc, s_w);
+        if (threadIdx.x == 0) out[8 * r + k] = tot;
     }
-    if (threadIdx.x < 8) out[8 * r + threadIdx.x] = s[threadIdx.x][0];
 }
 
 // ------------------------------------------------------------- backward ----
@@ -161,9 +171,11 @@ __global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
             load64<PREC>(V, p, xi, yi, zi, ti);
             const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
             const int maxn = V.maxneigh;
-            const uint32_t *lp = V.nlist + (size_t)(p / A) * (size_t)(A * maxn) + (p % A) * T + sub;
-            for (int k = sub; k < cnt; k += T, lp += 32) {
-                const uint32_t e = *lp;
+            const int Q = V.vec;
+            for (int k = 0; k < cnt; ++k) {
+                // this thread's share of the list layout: entries r T Q + sub Q + q
+                if ((k / Q) % T != sub) continue;
+                const uint32_t e = V.nlist[list_index(p, k, T, Q, maxn)];
                 const int j = (int)(e & kIdxMask);
                 double xj, yj, zj;
                 int tj;
@@ -252,7 +264,7 @@ __global__ void k_neighbors_out(View V, int *counts, int *nbr, int cap) {
     const int c = V.ncount[p];
     counts[o] = c;
     for (int k = 0; k < c && k < cap; ++k) {
-        const uint32_t e = V.nlist[list_index(p, k, V.tpa, V.maxneigh)];
+        const uint32_t e = V.nlist[list_index(p, k, V.tpa, V.vec, V.maxneigh)];
         nbr[o * cap + k] = V.id[e & kIdxMask];
     }
 }
@@ -280,6 +292,7 @@ cudaError_t launch_state_out(const View &V, double *x, double *v, double *f, cud
 }
 
 cudaError_t launch_ev_reduce(const View &V, double *out, cudaStream_t s) {
+    k_ev_tiles<<<grid_of(V.n_tiles * 32, 256), 256, 0, s>>>(V);
     k_ev_reduce<<<V.n_rep, 256, 0, s>>>(V, out);
     return cudaGetLastError();
 }

@@ -189,6 +189,22 @@ static md_status read_ctl(md_system *h, Ctl *c) {
     return MD_OK;
 }
 
+// list statistics summed over replicas (synchronises)
+static md_status read_stats(md_system *h, int *max_count, long long *entries) {
+    std::vector<int> mc(h->n_rep);
+    std::vector<unsigned long long> en(h->n_rep);
+    CK(h, cudaMemcpyAsync(mc.data(), h->V.rep_maxcnt, sizeof(int) * h->n_rep, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(en.data(), h->V.rep_entries, sizeof(unsigned long long) * h->n_rep, cudaMemcpyDeviceToHost,
+                          h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    int m = 0;
+    long long e = 0;
+    for (int r = 0; r < h->n_rep; ++r) { m = std::max(m, mc[r]); e += (long long)en[r]; }
+    *max_count = m;
+    *entries = e;
+    return MD_OK;
+}
+
 static md_status alloc_list(md_system *h, int maxn) {
     dfree(h, h->V.nlist);
     h->V.nlist = nullptr;
@@ -217,7 +233,7 @@ static md_status settle_overflow(md_system *h, bool all) {
         if (st) return st;
         if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity");
         if (!(c.err & kErrOverflow)) return MD_OK;
-        const int need = round_up((int)std::ceil(c.need_maxneigh * 1.2) + 8, 32);
+        const int need = round_up((int)std::ceil(c.need_maxneigh * 1.2) + 8, 128);
         st = alloc_list(h, need);
         if (st) return st;
         unsigned zero = 0;
@@ -333,7 +349,7 @@ static int initial_maxneigh(const std::vector<Rep> &reps, double rl) {
     double rho = 0;
     for (const Rep &r : reps) rho = std::max(rho, r.natoms / (r.L[0] * r.L[1] * r.L[2]));
     const double n = 4.18879020478639 * rl * rl * rl * rho;
-    return round_up((int)std::ceil(1.4 * n) + 16, 32);
+    return round_up((int)std::ceil(1.4 * n) + 16, 128);
 }
 
 static md_status create_impl(int n_rep, const md_config *cfgs, const double *const *x, const double *const *v,
@@ -400,6 +416,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.ntypes = h->cfg.n_types;
     V.half = (h->cfg.list == MD_LIST_HALF) ? 1 : 0;
     V.tpa = h->cfg.tpa ? h->cfg.tpa : 1;
+    V.vec = V.tpa <= 8 ? 4 : 1;
     V.dt = h->cfg.dt;
     V.rc2 = h->cfg.cutoff * h->cfg.cutoff;
     V.rl2 = rl * rl;
@@ -430,6 +447,12 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.tile_rep = d_tile_rep;
     AL(V.rep_disp, (size_t)n_rep);
     AL(V.rep_flag, (size_t)n_rep);
+    AL(V.rep_maxcnt, (size_t)n_rep);
+    AL(V.rep_entries, (size_t)n_rep);
+    int *d_bin_rep;
+    AL(d_bin_rep, (size_t)V.nbins_total);
+    V.bin_rep = d_bin_rep;
+    AL(V.ev_tile, (size_t)V.n_tiles * 8);
     if (V.prec == MD_PREC_FP64) AL(V.pos4, n);
     else AL(V.xr, 3 * n);
     AL(V.v, 3 * n);
@@ -464,9 +487,11 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
         md_status st = alloc_list(h, initial_maxneigh(h->reps, rl));
         if (st) { md_destroy(h); return st; }
     }
-    std::vector<int> tile_rep(V.n_tiles);
-    for (int r = 0; r < n_rep; ++r)
+    std::vector<int> tile_rep(V.n_tiles), bin_rep(V.nbins_total);
+    for (int r = 0; r < n_rep; ++r) {
         for (int t = 0; t < h->reps[r].ntiles; ++t) tile_rep[h->reps[r].tile0 + t] = r;
+        for (int b = 0; b < h->reps[r].nbins; ++b) bin_rep[h->reps[r].bin0 + b] = r;
+    }
     // validate types on the host (one copy at creation)
     for (int r = 0; r < n_rep; ++r) {
         std::vector<int32_t> ht((size_t)cfgs[r].n_atoms);
@@ -491,6 +516,9 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     } while (0)
     CKD(cudaMemcpyAsync(d_rep, h->reps.data(), sizeof(Rep) * n_rep, cudaMemcpyHostToDevice, h->s));
     CKD(cudaMemcpyAsync(d_tile_rep, tile_rep.data(), sizeof(int) * V.n_tiles, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemcpyAsync(d_bin_rep, bin_rep.data(), sizeof(int) * V.nbins_total, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemsetAsync(V.rep_maxcnt, 0, sizeof(int) * n_rep, h->s));
+    CKD(cudaMemsetAsync(V.rep_entries, 0, sizeof(unsigned long long) * n_rep, h->s));
     CKD(cudaMemsetAsync(V.rep_disp, 0, sizeof(unsigned) * n_rep, h->s));
     CKD(cudaMemsetAsync(V.rep_flag, 0, sizeof(int) * n_rep, h->s));
     CKD(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->s));
@@ -604,6 +632,26 @@ md_status md_step(md_system *h, int64_t nsteps) {
     return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: too many overflow recoveries");
 }
 
+md_status md_step_eager(md_system *h, int64_t nsteps) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    if (nsteps < 0 || nsteps > (int64_t)0x7fffffff) return fail(h, MD_ERR_INVALID, "bad nsteps");
+    if (nsteps == 0) return MD_OK;
+    int rem = (int)nsteps, first = 1;
+    CK(h, cudaMemcpyAsync(&h->d_ctl->remaining, &rem, sizeof(int), cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(&h->d_ctl->first, &first, sizeof(int), cudaMemcpyHostToDevice, h->s));
+    std::vector<KCall> seq;
+    drift_sequence(h->V, false, seq);
+    rebuild_sequence(h->V, false, false, seq);
+    force_sequence(h->V, kModeStep, h->block, false, seq);
+    for (int64_t k = 0; k < nsteps; ++k) CK(h, run_seq(h, seq));
+    Ctl c;
+    md_status st = read_ctl(h, &c);
+    if (st) return st;
+    if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity in md_step_eager");
+    if (c.err & kErrOverflow) return fail(h, MD_ERR_LIST_OVERFLOW, "list overflow in md_step_eager (use md_step)");
+    return MD_OK;
+}
+
 md_status md_energy_virial(md_system *h, double *out) {
     if (!h || !out) return fail(h, MD_ERR_INVALID, "null argument");
     md_status st = compute_forces(h, kModeEV);
@@ -670,7 +718,7 @@ md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x,
     return MD_OK;
 }
 
-md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block) {
+md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block, int32_t vec) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
     if (tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
         return fail(h, MD_ERR_INVALID, "tpa must be 1,2,4,8,16 or 32");
@@ -678,10 +726,12 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
     if (list == MD_LIST_HALF && h->cfg.pot != MD_POT_LJ)
         return fail(h, MD_ERR_UNSUPPORTED, "half lists are implemented for LJ only");
     if (block != 64 && block != 128 && block != 256) return fail(h, MD_ERR_INVALID, "block must be 64, 128 or 256");
+    if (vec != 1 && vec != 4) return fail(h, MD_ERR_INVALID, "vec must be 1 or 4");
     const int half = list == MD_LIST_HALF ? 1 : 0;
-    const bool relayout = (tpa != h->V.tpa) || (half != h->V.half);
+    const bool relayout = (tpa != h->V.tpa) || (half != h->V.half) || (vec != h->V.vec);
     h->V.tpa = tpa;
     h->V.half = half;
+    h->V.vec = vec;
     h->block = block;
     drop_graph(h);
     if (relayout) return md_build_neighbors(h);
@@ -690,10 +740,11 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
 
 md_status md_autotune(md_system *h, const char *cache_path) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
-    Ctl c;
-    md_status st = read_ctl(h, &c);
+    int mc = 0;
+    long long entries = 0;
+    md_status st = read_stats(h, &mc, &entries);
     if (st) return st;
-    const double avg = h->n_real > 0 ? (double)c.list_entries / (double)h->n_real : 0.0;
+    const double avg = h->n_real > 0 ? (double)entries / (double)h->n_real : 0.0;
     char key[256];
     snprintf(key, sizeof(key), "pot=%d prec=%d n=%lld nrep=%d nbr=%d list=%d", (int)h->cfg.pot, (int)h->cfg.prec,
              (long long)h->n_real, h->n_rep, (int)std::lround(avg), (int)h->cfg.list);
@@ -703,9 +754,9 @@ md_status md_autotune(md_system *h, const char *cache_path) {
         while (std::getline(in, line)) {
             const size_t bar = line.find('|');
             if (bar == std::string::npos || line.substr(0, bar) != key) continue;
-            int t = 0, l = 0, b = 0;
-            if (sscanf(line.c_str() + bar + 1, "%d %d %d", &t, &l, &b) == 3)
-                return md_set_kernel(h, t, (md_listkind)l, b);
+            int t = 0, l = 0, b = 0, q = 0;
+            if (sscanf(line.c_str() + bar + 1, "%d %d %d %d", &t, &l, &b, &q) == 4)
+                return md_set_kernel(h, t, (md_listkind)l, b, q);
         }
     }
     std::vector<int> lists;
@@ -716,11 +767,12 @@ md_status md_autotune(md_system *h, const char *cache_path) {
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     double best = 1e300;
-    int bt = 1, bl = MD_LIST_FULL, bb = 256;
+    int bt = 1, bl = MD_LIST_FULL, bb = 256, bq = 1;
     for (int l : lists)
         for (int t : {1, 2, 4, 8, 16, 32})
+            for (int q : {1, 4})
             for (int b : {128, 256}) {
-                st = md_set_kernel(h, t, (md_listkind)l, b);
+                st = md_set_kernel(h, t, (md_listkind)l, b, q);
                 if (st) {
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
@@ -740,15 +792,15 @@ md_status md_autotune(md_system *h, const char *cache_path) {
                     ms.push_back(m);
                 }
                 std::sort(ms.begin(), ms.end());
-                if (ms[2] < best) { best = ms[2]; bt = t; bl = l; bb = b; }
+                if (ms[2] < best) { best = ms[2]; bt = t; bl = l; bb = b; bq = q; }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    st = md_set_kernel(h, bt, (md_listkind)bl, bb);
+    st = md_set_kernel(h, bt, (md_listkind)bl, bb, bq);
     if (st) return st;
     if (cache_path) {
         std::ofstream outf(cache_path, std::ios::app);
-        outf << key << "|" << bt << " " << bl << " " << bb << " " << best << "\n";
+        outf << key << "|" << bt << " " << bl << " " << bb << " " << bq << " " << best << "\n";
     }
     return MD_OK;
 }
@@ -771,14 +823,15 @@ md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_o
     cudaEventDestroy(e1);
     *ms_out = (double)ms / reps;
     if (bytes_out) {
-        Ctl c;
-        md_status st = read_ctl(h, &c);
+        int mc = 0;
+        long long entries = 0;
+        md_status st = read_stats(h, &mc, &entries);
         if (st) return st;
         // per atom: record (FP32 16 B or FP64 32 B) + list length 4 B + v in/out 48 B
         // (+ F'_i 4/8 B and the list a second time for the EAM density pass)
         const double rec = h->V.prec == MD_PREC_FP64 ? 32.0 : 16.0;
         double per_atom = rec + 4.0 + 48.0;
-        double list = 4.0 * (double)c.list_entries;
+        double list = 4.0 * (double)entries;
         if (h->cfg.pot == MD_POT_EAM_FS) {
             per_atom += rec + 4.0 + 2.0 * (h->V.prec == MD_PREC_FP64 ? 8.0 : 4.0);
             list *= 2.0;
@@ -800,8 +853,13 @@ md_status md_info(md_system *h, md_info_t *out) {
     out->list = h->V.half ? MD_LIST_HALF : MD_LIST_FULL;
     out->block = h->block;
     out->maxneigh = h->V.maxneigh;
-    out->max_count = c.max_count;
-    out->list_entries = c.list_entries;
+    int mc = 0;
+    long long entries = 0;
+    st = read_stats(h, &mc, &entries);
+    if (st) return st;
+    out->max_count = mc;
+    out->list_entries = entries;
+    out->vec = h->V.vec;
     out->rebuilds = c.rebuilds;
     out->steps = c.steps;
     for (int a = 0; a < 3; ++a) out->bins[a] = h->reps[0].nb[a];
@@ -810,10 +868,11 @@ md_status md_info(md_system *h, md_info_t *out) {
 
 md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t cap) {
     if (!h || !counts || !nbr) return fail(h, MD_ERR_INVALID, "null argument");
-    Ctl c;
-    md_status st = read_ctl(h, &c);
+    int mc = 0;
+    long long entries = 0;
+    md_status st = read_stats(h, &mc, &entries);
     if (st) return st;
-    if (cap < c.max_count) return fail(h, MD_ERR_INVALID, "cap %d < longest list %d", cap, c.max_count);
+    if (cap < mc) return fail(h, MD_ERR_INVALID, "cap %d < longest list %d", cap, mc);
     CK(h, launch_neighbors_out(h->V, counts, nbr, cap, h->s));
     return MD_OK;
 }

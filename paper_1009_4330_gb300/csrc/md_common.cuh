@@ -16,10 +16,13 @@
 //     is the stencil offset of j's bin relative to i's bin.  The separation
 //     is then d = rec_i - rec_j - (dx hx, dy hy, dz hz), periodic images
 //     included, without any minimum-image arithmetic in the force loop;
-//   * list order is tiled for a thread group of T threads per atom: entry k of
-//     atom i sits at  (i / A) * A * maxneigh + (k / T) * 32 + (i % A) * T + k % T
-//     with A = 32 / T atoms per warp, so every warp-wide list load is one
-//     contiguous 128-byte line (T = 1 is the paper's column-major list).
+//   * list order is tiled for a thread group of T threads per atom, each
+//     thread loading Q consecutive entries at once (Q = 1 or 4): with
+//     A = 32 / T atoms per warp, entry k of atom i sits at
+//         (i / A) * A * maxneigh + (k / (T Q)) * 32 Q + ((i % A) T + (k / Q) % T) Q + k % Q,
+//     so every warp-wide list load is one contiguous 128 Q-byte block and a
+//     thread's Q entries arrive in one 4Q-byte load (T = Q = 1 is the paper's
+//     column-major list).  maxneigh is a multiple of 128.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -59,8 +62,6 @@ struct Ctl {                // device control block of a handle
     unsigned ticket_force;
     unsigned ticket_build;
     int need_maxneigh;      // largest list length seen by an overflowing build
-    int max_count;          // largest list length at the last build
-    long long list_entries; // entries written at the last build (all rebuilt replicas)
     long long steps;        // completed time steps
     long long rebuilds;     // completed replica builds
 };
@@ -83,6 +84,7 @@ struct PairTab {
 struct View {
     int n_pad, n_tiles, n_rep, nbins_total, maxneigh;
     int tpa;          // threads per atom the list is laid out for
+    int vec;          // entries per thread per list load (1 or 4)
     int half;         // 1: half list (each pair once, Newton-3 atomics)
     int prec;         // md_precision
     int pot;          // md_potential
@@ -91,8 +93,11 @@ struct View {
     float rc2f, rl2f_lo, rl2f_hi, skin_half2f;
     const Rep *rep;
     const int *tile_rep;
+    const int *bin_rep;   // replica of each global bin
     unsigned *rep_disp;   // per replica: max |x - x_build|^2 since the build, as float bits
     int *rep_flag;        // per replica: 1 = rebuild in this step
+    int *rep_maxcnt;      // per replica: longest list at its last build
+    unsigned long long *rep_entries;  // per replica: list entries at its last build
     // atom state, sorted order
     double *xr;           // [3][n_pad] cell-relative positions (mixed)
     double4_32a *pos4;        // [n_pad] cell-relative positions + type bits (fp64)
@@ -112,6 +117,7 @@ struct View {
     double *emb;          // F(rho) per atom (energy)
     // per-atom energy / virial for deterministic reductions: [8][n_pad]
     double *ev;
+    double *ev_tile;      // [n_tiles][8] per-tile partial sums
     // backward
     double *gs, *gx;      // [3][n_pad] gradient in / out (sorted)
     double *gp_part;      // per block partial parameter gradients
@@ -137,6 +143,22 @@ enum : int {
                        // used to time the force pass without changing the state
 };
 
+// ----------------------------------------------- block reductions (FP64) --
+// Fixed-order reduction of one double over a block of blockDim.x threads
+// (a multiple of 32): warp shuffles, then warp 0 sums the warps in order.
+// Returns the total in thread 0.
+__device__ __forceinline__ double block_sum(double x, double *s_warp) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s_warp[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_warp[k];
+    return t;
+}
+
 // ---------------------------------------------------------------- helpers --
 
 __device__ __forceinline__ int unpack_bx(int b) { return b & 1023; }
@@ -144,10 +166,11 @@ __device__ __forceinline__ int unpack_by(int b) { return (b >> 10) & 1023; }
 __device__ __forceinline__ int unpack_bz(int b) { return (b >> 20) & 1023; }
 __device__ __forceinline__ int pack_bins(int bx, int by, int bz) { return bx | (by << 10) | (bz << 20); }
 
-// list slot of entry k of atom p for a T-thread group layout
-__device__ __forceinline__ size_t list_index(int p, int k, int T, int maxn) {
+// list slot of entry k of atom p for a T-thread group layout with Q entries per load
+__device__ __forceinline__ size_t list_index(int p, int k, int T, int Q, int maxn) {
     const int A = 32 / T;
-    return (size_t)(p / A) * (size_t)(A * maxn) + (size_t)(k / T) * 32 + (size_t)(p % A) * T + (k % T);
+    return (size_t)(p / A) * (size_t)(A * maxn) + (size_t)(k / (T * Q)) * (32 * Q) +
+           (size_t)(((p % A) * T + (k / Q) % T) * Q) + (k % Q);
 }
 
 // stencil offset component (dx) from an entry field value c = dx + 1 in {0,1,2},

@@ -184,8 +184,9 @@ class System:
         self._call("md_compute_forces", _ptr(f))
         return f
 
-    def step(self, nsteps=1):
-        self._call("md_step", ctypes.c_int64(int(nsteps)))
+    def step(self, nsteps=1, eager=False):
+        """Advance nsteps velocity-Verlet steps (eager: without CUDA graphs, for profiling)."""
+        self._call("md_step_eager" if eager else "md_step", ctypes.c_int64(int(nsteps)))
 
     def energy_virial(self):
         """(n_rep, 8): Epot, Ekin, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz."""
@@ -238,8 +239,11 @@ class System:
     def autotune(self, cache_path=None):
         self._call("md_autotune", cache_path.encode() if cache_path else None)
 
-    def set_kernel(self, tpa, list="full", block=256):
-        self._call("md_set_kernel", ctypes.c_int32(tpa), _LIST[list], ctypes.c_int32(block))
+    def set_kernel(self, tpa, list="full", block=256, vec=None):
+        """Force-kernel variant; vec (list entries per thread per load) defaults to 4 for tpa <= 8, else 1."""
+        if vec is None:
+            vec = 4 if tpa <= 8 else 1
+        self._call("md_set_kernel", ctypes.c_int32(tpa), _LIST[list], ctypes.c_int32(block), ctypes.c_int32(vec))
 
     def sync_status(self):
         self._call("md_sync_status")

@@ -42,7 +42,7 @@ def test_struct_layout_matches_header():
     # md_config: 16 fields, pointer-aligned; the ctypes mirror must have the C size
     from paper_1009_4330_gb300 import _lib
     assert ctypes.sizeof(_lib.MdConfig) == 128
-    assert ctypes.sizeof(_lib.MdInfo) == 72
+    assert ctypes.sizeof(_lib.MdInfo) == 80
 
 
 def test_null_arguments_are_rejected_without_device_work(lib):

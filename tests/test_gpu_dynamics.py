@@ -48,6 +48,20 @@ def test_step_calls_compose():
     assert np.abs(va - vb).max() < 1e-11
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eager_step_equals_graph_step(prec):
+    d = lj_case(7, 0.05, seed=14)
+    with lj_system(d, prec, 2) as a, lj_system(d, prec, 2) as b:
+        a.step(35)
+        b.step(35, eager=True)
+        ia, ib = a.info(), b.info()
+        sa = [t.cpu().numpy() for t in a.state()]
+        sb = [t.cpu().numpy() for t in b.state()]
+    assert ia["steps"] == ib["steps"] == 35 and ia["rebuilds"] == ib["rebuilds"]
+    for u, w in zip(sa, sb):
+        assert np.array_equal(u, w)
+
+
 def test_mixed_trajectory_tracks_oracle_short():
     d = lj_case(8, 0.05, seed=21)
     ref = oracle.nve(d["x"], d["v"], d["box"], 20, DT, RC, SKIN)

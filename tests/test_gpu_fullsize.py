@@ -40,8 +40,8 @@ def test_lj864k_mixed_all_layouts(lj864k):
     with System.lj(d["x"], d["v"], d["box"], cutoff=d["rc"], skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
                    tpa=1) as s:
         for k, tpa in enumerate(TPAS):
-            for lst in ("full", "half"):
-                s.set_kernel(tpa, lst, 256)
+            for lst, vec in (("full", 1), ("full", 4), ("half", 4 if tpa <= 8 else 1)):
+                s.set_kernel(tpa, lst, 256, vec)
                 f = s.compute_forces().cpu().numpy()
                 assert rel_maxnorm(f[idx], d["f"]) < TOL_MIXED, (tpa, lst)
                 if lst == "full" and k in (0, 5):
@@ -61,20 +61,19 @@ def test_lj864k_fp64(lj864k):
     assert rel_maxnorm(f[d["idx"]], d["f"]) < TOL_FP64
 
 
-def test_lj864k_steps_keep_parity(lj864k):
-    # after the bench's own step loop (with in-graph rebuilds), the forces the
-    # library holds are those of its positions, checked on the sample
+def test_lj864k_steps_keep_parity():
+    # the benchmark input itself (fcc + Maxwell-Boltzmann at T = 1.44): after
+    # the step loop with in-graph rebuilds, the forces the library holds are
+    # those of its positions, checked on a sample
     from paper_1009_4330_gb300 import System
-    d = lj864k
-    if d["rc"] != 2.5:
-        pytest.skip("one cutoff is enough for the stepping check")
-    with System.lj(d["x"], d["v"], d["box"], cutoff=d["rc"], skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
+    d = synth.config1(rc=2.5)
+    with System.lj(d["x"], d["v"], d["box"], cutoff=2.5, skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
                    tpa=4) as s:
         s.step(60)
         x, _, f = (a.cpu().numpy() for a in s.state())
         assert s.info()["rebuilds"] >= 2
-    idx = d["idx"]
-    fr, _, _ = oracle.lj_at(x, d["box"], d["rc"], idx)
+    idx = sample(x.shape[0], 32, seed=9)
+    fr, _, _ = oracle.lj_at(x, d["box"], 2.5, idx)
     assert rel_maxnorm(f[idx], fr) < TOL_MIXED
 
 
