@@ -89,7 +89,11 @@ __device__ __forceinline__ double group_sum(double x) {
 // thread's Q entries arriving in one (vector) load, the next round's load
 // issued before this round's work; the Q records are gathered before any
 // arithmetic so that Q gathers are in flight.  For each entry calls
-// pair(e, dx, dy, dz, r2, tj) with d = x_i - x_j (periodic image included).
+// pair(e, dx, dy, dz, r2, tj) with d = x_i - x_j (periodic image included),
+// bracketed per round by pair.round_begin() / pair.round_end(): the pair
+// terms of one round (at most Q) are summed plainly and the round's sum is
+// added to the running total with compensation (blocked Kahan summation:
+// error ~ (Q + 2) u sum |terms| instead of ~n u for n plain additions).
 template <int PREC, int T, int Q, class Pair>
 __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int sub, int cnt,
                                           typename Pol<PREC>::real xi, typename Pol<PREC>::real yi,
@@ -99,6 +103,7 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
     using real = typename P::real;
     constexpr int PER = T * Q;
     const int nr = (cnt + PER - 1) / PER;
+    const real hy4 = hy * (real)0.25, hz16 = hz * (real)0.0625;  // exact: powers of two
     uint32_t cur[Q], nxt[Q];
     if (nr > 0) {
         if (Q == 4) {
@@ -123,19 +128,21 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
         int tj[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            if (q < left) P::load(V, (int)(cur[q] & kIdxMask), xj[q], yj[q], zj[q], tj[q]);
+            if (q < left) P::load(V, entry_j(cur[q]), xj[q], yj[q], zj[q], tj[q]);
         }
+        pair.round_begin();
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (q < left) {
                 const uint32_t e = cur[q];
-                const real dx = fma(-(real)code_delta(e, 26), hx, xi - xj[q]);
-                const real dy = fma(-(real)code_delta(e, 28), hy, yi - yj[q]);
-                const real dz = fma(-(real)code_delta(e, 30), hz, zi - zj[q]);
+                const real dx = fma(-(real)code_x(e), hx, xi - xj[q]);
+                const real dy = fma(-(real)code_y4(e), hy4, yi - yj[q]);
+                const real dz = fma(-(real)code_z16(e), hz16, zi - zj[q]);
                 const real r2 = dx * dx + dy * dy + dz * dz;
                 pair(e, dx, dy, dz, r2, tj[q]);
             }
         }
+        pair.round_end();
 #pragma unroll
         for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
     }
@@ -198,6 +205,9 @@ struct LJPair {
     int ti, nt, n;
     Acc ax, ay, az, e;
     Acc w[6];
+    real rx, ry, rz;  // this round's plain partial sums
+    __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
+    __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int tj) {
         if (r2 < rc2) {
             const int tp = MT ? ti * nt + tj : 0;
@@ -205,9 +215,9 @@ struct LJPair {
             const real r6i = r2i * r2i * r2i;
             const real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
             const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
-            ax.add(fxp); ay.add(fyp); az.add(fzp);
+            rx += fxp; ry += fyp; rz += fzp;
             if (HALF) {
-                const int j = (int)(ent & kIdxMask);
+                const int j = entry_j(ent);
                 atomicAdd(&V->f[j], -(double)fxp);
                 atomicAdd(&V->f[n + j], -(double)fyp);
                 atomicAdd(&V->f[2 * n + j], -(double)fzp);
@@ -223,7 +233,7 @@ struct LJPair {
 };
 
 template <int PREC, int T, int Q, int HALF, int EV, int MT>
-__global__ void __launch_bounds__(256) k_lj(View V, KArgs a) {
+__global__ void __launch_bounds__(256, (PREC == MD_PREC_MIXED && !EV) ? 4 : 1) k_lj(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
     __shared__ real s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
@@ -343,12 +353,14 @@ template <int PREC>
 struct RhoPair {
     using real = typename Pol<PREC>::real;
     typename Pol<PREC>::Acc acc;
-    real rc, rc2;
+    real rc, rc2, part;
+    __device__ __forceinline__ void round_begin() { part = 0; }
+    __device__ __forceinline__ void round_end() { acc.add(part); }
     __device__ __forceinline__ void operator()(uint32_t, real, real, real, real r2, int) {
         if (r2 < rc2) {
             const real r = r2 * Pol<PREC>::rsqrt(r2);
             const real t = rc - r;
-            acc.add(t * t);
+            part += t * t;
         }
     }
 };
@@ -400,9 +412,12 @@ struct EamPair {
     real rc, rc2, c0, c1, c2, fpi;
     Acc ax, ay, az, e;
     Acc w[6];
+    real rx, ry, rz;
+    __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
+    __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int) {
         if (r2 < rc2) {
-            const real fpj = Pol<PREC>::fp(*V, (int)(ent & kIdxMask));
+            const real fpj = Pol<PREC>::fp(*V, entry_j(ent));
             const real rinv = Pol<PREC>::rsqrt(r2);
             const real r = r2 * rinv;
             const real t = rc - r;
@@ -411,7 +426,7 @@ struct EamPair {
             // -(phi' + (F'_i + F'_j) rho') / r with phi' = -2t poly + t^2 dpoly, rho' = -2t
             const real coef = -t * ((real)-2 * poly + t * dpoly - (real)2 * (fpi + fpj)) * rinv;
             const real fxp = dx * coef, fyp = dy * coef, fzp = dz * coef;
-            ax.add(fxp); ay.add(fyp); az.add(fzp);
+            rx += fxp; ry += fyp; rz += fzp;
             if (EV) {
                 e.add((real)0.5 * t * t * poly);
                 w[0].add((real)0.5 * dx * fxp); w[1].add((real)0.5 * dy * fyp); w[2].add((real)0.5 * dz * fzp);

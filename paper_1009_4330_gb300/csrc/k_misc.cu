@@ -175,14 +175,14 @@ __global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
             for (int k = 0; k < cnt; ++k) {
                 // this thread's share of the list layout: entries r T Q + sub Q + q
                 if ((k / Q) % T != sub) continue;
-                const uint32_t e = V.nlist[list_index(p, k, T, Q, maxn)];
-                const int j = (int)(e & kIdxMask);
+                const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, maxn)];
+                const int j = entry_j(e);
                 double xj, yj, zj;
                 int tj;
                 load64<PREC>(V, j, xj, yj, zj, tj);
-                const double dx = xi - xj - (double)code_delta(e, 26) * R.h[0];
-                const double dy = yi - yj - (double)code_delta(e, 28) * R.h[1];
-                const double dz = zi - zj - (double)code_delta(e, 30) * R.h[2];
+                const double dx = xi - xj - entry_dx(e) * R.h[0];
+                const double dy = yi - yj - entry_dy(e) * R.h[1];
+                const double dz = zi - zj - entry_dz(e) * R.h[2];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < V.rc2)) continue;
                 const int tp = ti * nt + tj;
@@ -264,8 +264,8 @@ __global__ void k_neighbors_out(View V, int *counts, int *nbr, int cap) {
     const int c = V.ncount[p];
     counts[o] = c;
     for (int k = 0; k < c && k < cap; ++k) {
-        const uint32_t e = V.nlist[list_index(p, k, V.tpa, V.vec, V.maxneigh)];
-        nbr[o * cap + k] = V.id[e & kIdxMask];
+        const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, V.maxneigh)];
+        nbr[o * cap + k] = V.id[entry_j(e)];
     }
 }
 

@@ -100,22 +100,17 @@ __global__ void k_prepare(View V, KArgs a) {
     V.slot[p] = atomicAdd(&V.bin_count[gb], 1);
 }
 
-// Exclusive scan of each rebuilding replica's bin counts (one block per
-// replica): bin_start[b] = first slot of bin b.
-__global__ void k_scan(View V, KArgs a) {
-    __shared__ int s_warp[32];
-    const int r = blockIdx.x;
-    if (!a.all && !V.rep_flag[r]) return;
-    const int bin0 = V.rep[r].bin0, nb = V.rep[r].nbins, base = V.rep[r].atom0;
-    const int per = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = min(threadIdx.x * per, nb), b1 = min(b0 + per, nb);
-    int s = 0;
-    for (int b = b0; b < b1; ++b) s += V.bin_count[bin0 + b];
-    // block-wide exclusive scan of s
+// bin_start[b] = first slot of bin b: an exclusive scan of the bin counts,
+// segmented per replica (each replica's slots start at its atom0), in three
+// parallel passes.  Bins of replicas that are not rebuilding get meaningless
+// values, which nothing reads before their next rebuild.
+constexpr int kScanBlock = 4096;  // bins per block of k_scan1 (1024 threads x 4)
+
+__device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = s;
+    int inc = v;
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) s_warp[w] = inc;
@@ -124,18 +119,63 @@ __global__ void k_scan(View V, KArgs a) {
         const int nw = blockDim.x >> 5;
         int t = lane < nw ? s_warp[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, t, o);
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
-        if (lane < nw) s_warp[lane] = t;  // inclusive over warps
+        if (lane < nw) s_warp[lane] = t;
     }
     __syncthreads();
-    int run = inc - s + (w > 0 ? s_warp[w - 1] : 0);
-    for (int b = b0; b < b1; ++b) {
-        const int c = V.bin_count[bin0 + b];
-        V.bin_start[bin0 + b] = base + run;
-        run += c;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    const int r = inc - v + (w > 0 ? s_warp[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// pass 1: prefix inside each block of 4096 bins, and the block totals
+__global__ void k_scan1(View V, KArgs a) {
+    __shared__ int s_warp[32];
+    const int b0 = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    int c[4], sum = 0;
+    for (int k = 0; k < 4; ++k) {
+        c[k] = (b0 + k < V.nbins_total) ? V.bin_count[b0 + k] : 0;
+        sum += c[k];
     }
+    int total;
+    int run = block_excl_scan(sum, s_warp, &total);
+    for (int k = 0; k < 4; ++k) {
+        if (b0 + k < V.nbins_total) V.bin_start[b0 + k] = run;
+        run += c[k];
+    }
+    if (threadIdx.x == 0) V.scan_blk[blockIdx.x] = total;
+}
+
+// pass 2 (one block): exclusive scan of the block totals; per-replica bases
+__global__ void k_scan2(View V, KArgs a) {
+    __shared__ int s_warp[32];
+    const int nblk = (V.nbins_total + kScanBlock - 1) / kScanBlock;
+    int carry = 0;
+    for (int c0 = 0; c0 < nblk; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < nblk ? V.scan_blk[i] : 0;
+        int total;
+        const int ex = block_excl_scan(v, s_warp, &total);
+        if (i < nblk) V.scan_blk[i] = carry + ex;
+        carry += total;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < V.n_rep; r += blockDim.x) {
+        const int b = V.rep[r].bin0;
+        V.rep_base[r] = V.scan_blk[b / kScanBlock] + V.bin_start[b] - V.rep[r].atom0;
+    }
+}
+
+// pass 3: global prefix, rebased to each rebuilding replica's first slot
+__global__ void k_scan3(View V, KArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= V.nbins_total) return;
+    const int r = V.bin_rep[b];
+    if (!a.all && !V.rep_flag[r]) return;
+    V.bin_start[b] += V.scan_blk[b / kScanBlock] - V.rep_base[r];
 }
 
 // perm[bin_start[bin] + arrival slot] = old slot
@@ -198,17 +238,38 @@ __global__ void k_gather(View V, KArgs a) {
     V.recb[dst] = rr;
 }
 
+// Exact FP64 list test for a pair inside the FP32 margin band (rare; kept
+// out of line so that it does not cost the main loop registers).
+template <int PREC>
+__device__ __noinline__ bool in_list_fp64(const View &V, const Rep &R, int p, int j, int dx, int dy, int dz) {
+    double xi[3], xj[3];
+    if (PREC == MD_PREC_FP64) {
+        const double4_32a qi = V.pos4[p], qj = V.pos4[j];
+        xi[0] = qi.x; xi[1] = qi.y; xi[2] = qi.z;
+        xj[0] = qj.x; xj[1] = qj.y; xj[2] = qj.z;
+    } else {
+        const int n = V.n_pad;
+        for (int q = 0; q < 3; ++q) { xi[q] = V.xr[q * n + p]; xj[q] = V.xr[q * n + j]; }
+    }
+    const double d0 = xi[0] - xj[0] - dx * R.h[0];
+    const double d1 = xi[1] - xj[1] - dy * R.h[1];
+    const double d2 = xi[2] - xj[2] - dz * R.h[2];
+    return d0 * d0 + d1 * d1 + d2 * d2 < V.rl2;
+}
+
 // Verlet list of every atom of a rebuilding replica: all j in the 27 cells
 // around i's cell with |x_i - x_j| < rl.  One warp per home cell, one lane
-// per home atom; the warp walks the 27 neighbour cells, stages 32 candidate
-// records at a time in shared memory (one coalesced load) and every lane
-// tests every staged candidate against its atom (a broadcast read), so
-// lanes never diverge on loop bounds.  The test is FP32 on the cell-relative
-// records with a margin far above their rounding error; pairs inside the
-// margin band are decided in FP64, so the list equals the FP64 definition
-// exactly.  HALF keeps j > i only (each pair once).
+// per home atom.  The 27 neighbour cells form 9 rows of 3 x-adjacent cells;
+// lanes 0..26 fetch the 27 cell bounds at once, and each row is walked as one
+// flat candidate range in chunks of 32: every lane stages one candidate
+// record, already shifted into the home cell's frame and carrying its list
+// entry (index | stencil code) in .w, into shared memory, then every lane
+// tests every staged candidate against its own atom (broadcast reads; no
+// divergence on loop bounds).  The test is FP32 with a margin far above its
+// rounding error; pairs inside the margin band are decided in FP64, so the
+// list equals the FP64 definition exactly.  HALF keeps j > i only.
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(256) k_build(View V, KArgs a) {
+__global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
     __shared__ float4 s_c[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gb = blockIdx.x * 8 + w;
@@ -220,67 +281,77 @@ __global__ void __launch_bounds__(256) k_build(View V, KArgs a) {
         my_rep = r;
         if (a.all || V.rep_flag[r]) {
             const Rep &R = V.rep[r];
-            const int n = V.n_pad, maxn = V.maxneigh, T = V.tpa, Q = V.vec;
+            const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
             const int lb = gb - R.bin0;
             const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
             const int bx = lb % nbx, by = (lb / nbx) % nby, bz = lb / (nbx * nby);
             const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
+            // neighbour cell (row = lane / 3, dx = lane % 3 - 1) bounds, one lane each
+            int my_st = 0, my_ct = 0;
+            if (lane < 27) {
+                const int row = lane / 3;
+                const int dx = lane - 3 * row - 1, dy = row % 3 - 1, dz = row / 3 - 1;
+                int cx = bx + dx, cy = by + dy, cz = bz + dz;
+                cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
+                cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
+                cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
+                const int nbin = R.bin0 + (cz * nby + cy) * nbx + cx;
+                my_st = V.bin_start[nbin];
+                my_ct = V.bin_count[nbin];
+            }
             const int hs = V.bin_start[gb], hn = V.bin_count[gb];
             const float lo = V.rl2f_lo, hi = V.rl2f_hi;
+
             for (int h0 = 0; h0 < hn; h0 += 32) {
                 const int p = hs + h0 + lane;
                 const bool act = (h0 + lane) < hn;
                 const float4 ri = act ? V.rec[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const uint32_t self_e = ((uint32_t)p << 6) | kSelfCode;
                 int cnt = 0;
-                for (int dz = -1; dz <= 1; ++dz) {
-                    int cz = bz + dz;
-                    cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        int cy = by + dy;
-                        cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            int cx = bx + dx;
-                            cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
-                            const int nbin = R.bin0 + (cz * nby + cy) * nbx + cx;
-                            const int s = V.bin_start[nbin], m = V.bin_count[nbin];
-                            const bool self_cell = (dx == 0 && dy == 0 && dz == 0);
-                            const uint32_t code = ((uint32_t)(dx + 1) << 26) | ((uint32_t)(dy + 1) << 28) |
-                                                  ((uint32_t)(dz + 1) << 30);
-                            // atom i seen from the neighbour cell's frame
-                            const float rx = ri.x - dx * hx, ry = ri.y - dy * hy, rz = ri.z - dz * hz;
-                            for (int c0 = 0; c0 < m; c0 += 32) {
-                                const int mm = min(32, m - c0);
-                                __syncwarp();
-                                if (lane < mm) s_c[w][lane] = V.rec[s + c0 + lane];
-                                __syncwarp();
-                                for (int c = 0; c < mm; ++c) {
-                                    const float4 rj = s_c[w][c];
-                                    const float ddx = rx - rj.x, ddy = ry - rj.y, ddz = rz - rj.z;
-                                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                                    const int j = s + c0 + c;
-                                    if (!act || r2 >= hi) continue;
-                                    if (self_cell && j == p) continue;
-                                    if (HALF && j <= p) continue;
-                                    bool in = r2 < lo;
-                                    if (!in) {  // margin band: decide in FP64
-                                        double xi[3], xj[3];
-                                        if (PREC == MD_PREC_FP64) {
-                                            const double4_32a qi = V.pos4[p], qj = V.pos4[j];
-                                            xi[0] = qi.x; xi[1] = qi.y; xi[2] = qi.z;
-                                            xj[0] = qj.x; xj[1] = qj.y; xj[2] = qj.z;
-                                        } else {
-                                            for (int q = 0; q < 3; ++q) { xi[q] = V.xr[q * n + p]; xj[q] = V.xr[q * n + j]; }
-                                        }
-                                        const double d0 = xi[0] - xj[0] - dx * R.h[0];
-                                        const double d1 = xi[1] - xj[1] - dy * R.h[1];
-                                        const double d2 = xi[2] - xj[2] - dz * R.h[2];
-                                        in = d0 * d0 + d1 * d1 + d2 * d2 < V.rl2;
-                                    }
-                                    if (in) {
-                                        if (cnt < maxn) V.nlist[list_index(p, cnt, T, Q, maxn)] = (uint32_t)j | code;
-                                        ++cnt;
-                                    }
-                                }
+#pragma unroll 1
+                for (int row = 0; row < 9; ++row) {
+                    const int n0 = __shfl_sync(0xffffffffu, my_ct, 3 * row);
+                    const int n1 = __shfl_sync(0xffffffffu, my_ct, 3 * row + 1);
+                    const int n2 = __shfl_sync(0xffffffffu, my_ct, 3 * row + 2);
+                    const int s0 = __shfl_sync(0xffffffffu, my_st, 3 * row);
+                    const int s1 = __shfl_sync(0xffffffffu, my_st, 3 * row + 1);
+                    const int s2 = __shfl_sync(0xffffffffu, my_st, 3 * row + 2);
+                    const int m = n0 + n1 + n2;
+                    const int dy = row % 3 - 1, dz = row / 3 - 1;
+                    const float oy = dy * hy, oz = dz * hz;
+                    const uint32_t rcode = ((uint32_t)(dz + 1) << 4) | ((uint32_t)(dy + 1) << 2);
+#pragma unroll 1
+                    for (int c0 = 0; c0 < m; c0 += 32) {
+                        const int f = c0 + lane;
+                        float4 st4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
+                        if (f < m) {
+                            const int seg = (f >= n0) + (f >= n0 + n1);
+                            const int j = seg == 0 ? s0 + f : (seg == 1 ? s1 + f - n0 : s2 + f - n0 - n1);
+                            const float4 rj = V.rec[j];
+                            const int dx = seg - 1;
+                            const uint32_t e = ((uint32_t)j << 6) | (uint32_t)seg | rcode;
+                            st4 = make_float4(rj.x + dx * hx, rj.y + oy, rj.z + oz, __uint_as_float(e));
+                        }
+                        __syncwarp();
+                        s_c[w][lane] = st4;
+                        __syncwarp();
+                        const int mm = min(32, m - c0);
+#pragma unroll 4
+                        for (int c = 0; c < mm; ++c) {
+                            const float4 q = s_c[w][c];
+                            const float ddx = ri.x - q.x, ddy = ri.y - q.y, ddz = ri.z - q.z;
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            if (!act || r2 >= hi) continue;
+                            const uint32_t e = __float_as_uint(q.w);
+                            if (e == self_e) continue;
+                            if (HALF && entry_j(e) <= p) continue;
+                            bool in = r2 < lo;
+                            if (!in) {
+                                in = in_list_fp64<PREC>(V, R, p, entry_j(e), entry_dx(e), dy, dz);
+                            }
+                            if (in) {
+                                if (cnt < maxn) V.nlist[list_index(p, cnt, lt, lq, maxn)] = e;
+                                ++cnt;
                             }
                         }
                     }
@@ -346,7 +417,10 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_prepare<MD_PREC_FP64>
                                                : (const void *)k_prepare<MD_PREC_MIXED>,
                         dim3(nb), dim3(256), 0, ap});
-    seq.push_back(KCall{(const void *)k_scan, dim3(V.n_rep), dim3(1024), 0, a});
+    const int nblk = (V.nbins_total + kScanBlock - 1) / kScanBlock;
+    seq.push_back(KCall{(const void *)k_scan1, dim3(nblk), dim3(1024), 0, a});
+    seq.push_back(KCall{(const void *)k_scan2, dim3(1), dim3(1024), 0, a});
+    seq.push_back(KCall{(const void *)k_scan3, dim3((V.nbins_total + 255) / 256), dim3(256), 0, a});
     seq.push_back(KCall{(const void *)k_scatter, dim3(nb), dim3(256), 0, a});
     seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_gather<MD_PREC_FP64>
                                                : (const void *)k_gather<MD_PREC_MIXED>,

@@ -216,6 +216,12 @@ static md_status alloc_list(md_system *h, int maxn) {
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+static int ilog2(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
 // run the list build kernel again (after growing the list)
 static md_status rebuild_list_only(md_system *h, bool all) {
     std::vector<KCall> seq;
@@ -417,6 +423,8 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.half = (h->cfg.list == MD_LIST_HALF) ? 1 : 0;
     V.tpa = h->cfg.tpa ? h->cfg.tpa : 1;
     V.vec = V.tpa <= 8 ? 4 : 1;
+    V.ltpa = ilog2(V.tpa);
+    V.lvec = ilog2(V.vec);
     V.dt = h->cfg.dt;
     V.rc2 = h->cfg.cutoff * h->cfg.cutoff;
     V.rl2 = rl * rl;
@@ -471,6 +479,8 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.perm, n);
     AL(V.bin_count, (size_t)V.nbins_total);
     AL(V.bin_start, (size_t)V.nbins_total + 1);
+    AL(V.scan_blk, (size_t)(V.nbins_total + 4095) / 4096 + 1);
+    AL(V.rep_base, (size_t)n_rep);
     AL(V.ncount, n);
     if (V.pot == MD_POT_EAM_FS) {
         if (V.prec == MD_PREC_FP64) AL(V.fp64, n);
@@ -732,6 +742,8 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
     h->V.tpa = tpa;
     h->V.half = half;
     h->V.vec = vec;
+    h->V.ltpa = ilog2(tpa);
+    h->V.lvec = ilog2(vec);
     h->block = block;
     drop_graph(h);
     if (relayout) return md_build_neighbors(h);

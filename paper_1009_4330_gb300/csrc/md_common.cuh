@@ -12,10 +12,12 @@
 //     accuracy whatever the box size (absolute FP32 coordinates in a 100-sigma
 //     box would only give ~4e-6);
 //   * the neighbour list is a padded array nlist[n_pad * maxneigh] of 32-bit
-//     entries  j | (dx+1) << 26 | (dy+1) << 28 | (dz+1) << 30, where (dx,dy,dz)
+//     entries  j << 6 | (dz+1) << 4 | (dy+1) << 2 | (dx+1), where (dx,dy,dz)
 //     is the stencil offset of j's bin relative to i's bin.  The separation
 //     is then d = rec_i - rec_j - (dx hx, dy hy, dz hz), periodic images
-//     included, without any minimum-image arithmetic in the force loop;
+//     included, without any minimum-image arithmetic in the force loop; the
+//     codes sit in the low bits so that each decodes to an exact float with
+//     one mask-or and one add (see code_x/y/z);
 //   * list order is tiled for a thread group of T threads per atom, each
 //     thread loading Q consecutive entries at once (Q = 1 or 4): with
 //     A = 32 / T atoms per warp, entry k of atom i sits at
@@ -34,8 +36,8 @@ namespace md {
 
 constexpr int kMaxTypes = MD_MAX_TYPES;
 constexpr int kIdxBits = 26;
-constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 constexpr int kMaxAtoms = 1 << kIdxBits;
+constexpr uint32_t kSelfCode = 0x15u;  // dx = dy = dz = 0
 constexpr int kMaxBinsPerAxis = 1023;
 
 // status bits latched in Ctl::err (first error code is also kept in Ctl::code)
@@ -85,6 +87,7 @@ struct View {
     int n_pad, n_tiles, n_rep, nbins_total, maxneigh;
     int tpa;          // threads per atom the list is laid out for
     int vec;          // entries per thread per list load (1 or 4)
+    int ltpa, lvec;   // log2 of tpa and vec
     int half;         // 1: half list (each pair once, Newton-3 atomics)
     int prec;         // md_precision
     int pot;          // md_potential
@@ -108,6 +111,8 @@ struct View {
     double *tx, *tv;      // [3][n_pad] staged absolute positions / velocities (old order)
     int *ttype, *tid, *key, *slot, *perm;
     int *bin_count, *bin_start;
+    int *scan_blk;        // per 4096-bin block: exclusive prefix of the bin counts
+    int *rep_base;        // per replica: global prefix at its first bin minus its first slot
     // list
     uint32_t *nlist;
     int *ncount;
@@ -166,17 +171,32 @@ __device__ __forceinline__ int unpack_by(int b) { return (b >> 10) & 1023; }
 __device__ __forceinline__ int unpack_bz(int b) { return (b >> 20) & 1023; }
 __device__ __forceinline__ int pack_bins(int bx, int by, int bz) { return bx | (by << 10) | (bz << 20); }
 
-// list slot of entry k of atom p for a T-thread group layout with Q entries per load
-__device__ __forceinline__ size_t list_index(int p, int k, int T, int Q, int maxn) {
-    const int A = 32 / T;
-    return (size_t)(p / A) * (size_t)(A * maxn) + (size_t)(k / (T * Q)) * (32 * Q) +
-           (size_t)(((p % A) * T + (k / Q) % T) * Q) + (k % Q);
+// list slot of entry k of atom p for a T-thread group layout with Q entries
+// per load (T = 2^lt, Q = 2^lq; A = 32 / T atoms per warp)
+__device__ __forceinline__ size_t list_index(int p, int k, int lt, int lq, int maxn) {
+    const int la = 5 - lt;
+    const int A = 1 << la;
+    return (size_t)(p >> la) * (size_t)(A * maxn) + ((size_t)(k >> (lt + lq)) << (5 + lq)) +
+           (size_t)(((((p & (A - 1)) << lt) + ((k >> lq) & ((1 << lt) - 1))) << lq) + (k & ((1 << lq) - 1)));
 }
 
-// stencil offset component (dx) from an entry field value c = dx + 1 in {0,1,2},
-// as an exact float: magic-number conversion of a small integer
-__device__ __forceinline__ float code_delta(uint32_t e, int shift) {
-    return __int_as_float(0x4B400000u | ((e >> shift) & 3u)) - 12582913.0f;
+// list entry fields
+__device__ __forceinline__ int entry_j(uint32_t e) { return (int)(e >> 6); }
+__device__ __forceinline__ uint32_t make_entry(int j, int dx, int dy, int dz) {
+    return ((uint32_t)j << 6) | ((uint32_t)(dz + 1) << 4) | ((uint32_t)(dy + 1) << 2) | (uint32_t)(dx + 1);
+}
+__device__ __forceinline__ int entry_dx(uint32_t e) { return (int)(e & 3u) - 1; }
+__device__ __forceinline__ int entry_dy(uint32_t e) { return (int)((e >> 2) & 3u) - 1; }
+__device__ __forceinline__ int entry_dz(uint32_t e) { return (int)((e >> 4) & 3u) - 1; }
+
+// Stencil offsets as exact floats by the magic-number conversion of a small
+// integer: 2^23 + 2^22 has a zero low mantissa, so OR-ing the field into it
+// and subtracting (2^23 + 2^22 + field scale) gives dx, 4 dy, 16 dz exactly.
+// Multiply by h, h/4, h/16 respectively.
+__device__ __forceinline__ float code_x(uint32_t e) { return __int_as_float(0x4B400000u | (e & 0x3u)) - 12582913.0f; }
+__device__ __forceinline__ float code_y4(uint32_t e) { return __int_as_float(0x4B400000u | (e & 0xCu)) - 12582916.0f; }
+__device__ __forceinline__ float code_z16(uint32_t e) {
+    return __int_as_float(0x4B400000u | (e & 0x30u)) - 12582928.0f;
 }
 
 __device__ __forceinline__ float warp_max(float x) {
