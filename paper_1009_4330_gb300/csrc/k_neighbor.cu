@@ -97,7 +97,17 @@ __global__ void k_prepare(View V, KArgs a) {
     if (!finite) latch_error(V.ctl, kErrNonfinite);
     const int gb = R.bin0 + (bc[2] * R.nb[1] + bc[1]) * R.nb[0] + bc[0];
     V.key[p] = gb;
-    V.slot[p] = atomicAdd(&V.bin_count[gb], 1);
+    // atoms of a warp are mostly in one or two bins: one atomic per distinct
+    // bin, each lane taking its rank among the lanes of its bin
+    const unsigned active = __activemask();
+    const unsigned same = __match_any_sync(active, gb);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    const int rank = __popc(same & ((1u << lane) - 1));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&V.bin_count[gb], __popc(same));
+    base = __shfl_sync(same, base, leader);
+    V.slot[p] = base + rank;
 }
 
 // bin_start[b] = first slot of bin b: an exclusive scan of the bin counts,
@@ -178,14 +188,17 @@ __global__ void k_scan3(View V, KArgs a) {
     V.bin_start[b] += V.scan_blk[b / kScanBlock] - V.rep_base[r];
 }
 
-// perm[bin_start[bin] + arrival slot] = old slot
+// perm[bin_start[bin] + arrival slot] = old slot; sid = the atom ids in
+// the same (arrival) order, contiguous per bin for the ranking in k_gather
 __global__ void k_scatter(View V, KArgs a) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= V.n_pad) return;
     const int r = V.tile_rep[p >> 5];
     if (!a.all && !V.rep_flag[r]) return;
     if (p - V.rep[r].atom0 >= V.rep[r].natoms) return;
-    V.perm[V.bin_start[V.key[p]] + V.slot[p]] = p;
+    const int q = V.bin_start[V.key[p]] + V.slot[p];
+    V.perm[q] = p;
+    V.sid[q] = V.tid[p];
 }
 
 // Final slot = bin start + rank of the atom's id inside its bin (so the
@@ -213,9 +226,9 @@ __global__ void k_gather(View V, KArgs a) {
     const int src = V.perm[q];
     const int gb = V.key[src];
     const int s = V.bin_start[gb], cnt = V.bin_count[gb];
-    const int myid = V.tid[src];
+    const int myid = V.sid[q];
     int rank = 0;
-    for (int k = 0; k < cnt; ++k) rank += (V.tid[V.perm[s + k]] < myid);
+    for (int k = 0; k < cnt; ++k) rank += (V.sid[s + k] < myid);
     const int dst = s + rank;
     const int lb = gb - R.bin0;
     const int bc[3] = {lb % R.nb[0], (lb / R.nb[0]) % R.nb[1], lb / (R.nb[0] * R.nb[1])};
@@ -257,20 +270,38 @@ __device__ __noinline__ bool in_list_fp64(const View &V, const Rep &R, int p, in
     return d0 * d0 + d1 * d1 + d2 * d2 < V.rl2;
 }
 
+// 32 x 32 bit-matrix transpose across a warp: on entry lane r holds row r
+// (bit c = M[r][c]); on return lane c holds column c (bit r = M[r][c]).
+// Five butterfly stages of recursive 2x2 block swaps.
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sft = 16 >> k;
+        const unsigned m = masks[k];
+        const unsigned p = __shfl_xor_sync(0xffffffffu, x, sft);
+        x = (lane & sft) ? ((x & ~m) | ((p >> sft) & m)) : ((x & m) | ((p << sft) & ~m));
+    }
+    return x;
+}
+
 // Verlet list of every atom of a rebuilding replica: all j in the 27 cells
-// around i's cell with |x_i - x_j| < rl.  One warp per home cell, one lane
-// per home atom.  The 27 neighbour cells form 9 rows of 3 x-adjacent cells;
-// lanes 0..26 fetch the 27 cell bounds at once, and each row is walked as one
-// flat candidate range in chunks of 32: every lane stages one candidate
-// record, already shifted into the home cell's frame and carrying its list
-// entry (index | stencil code) in .w, into shared memory, then every lane
-// tests every staged candidate against its own atom (broadcast reads; no
-// divergence on loop bounds).  The test is FP32 with a margin far above its
-// rounding error; pairs inside the margin band are decided in FP64, so the
-// list equals the FP64 definition exactly.  HALF keeps j > i only.
+// around i's cell with |x_i - x_j| < rl.  One warp per home cell (home atoms
+// in chunks of 32).  The 27 neighbour cells form 9 rows of 3 x-adjacent
+// cells; lanes 0..26 fetch the 27 cell bounds at once.  Each row is walked as
+// one flat candidate range, 32 candidates at a time, one per lane, held in
+// registers already shifted into the home cell's frame.  Each lane tests its
+// candidate against every home atom (records broadcast from shared memory)
+// into a 32-bit acceptance mask; a warp bit-matrix transpose turns the
+// candidates' masks into each home atom's mask of accepted candidates, and
+// each home-atom lane appends them to its list in candidate order (warp
+// ballot/prefix compaction in transposed form: deterministic lists, no
+// divergent per-pair bookkeeping).  The test is FP32 with a margin far above
+// its rounding error; pairs inside the margin band are decided in FP64, so
+// the list equals the FP64 definition exactly.  HALF keeps j > i only.
 template <int PREC, int HALF>
 __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
-    __shared__ float4 s_c[8][32];
+    __shared__ float4 s_h[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gb = blockIdx.x * 8 + w;
     int my_max = 0;
@@ -282,6 +313,7 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
         if (a.all || V.rep_flag[r]) {
             const Rep &R = V.rep[r];
             const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
+            const int la = 5 - lt, ltq = lt + lq, tq = 1 << ltq;
             const int lb = gb - R.bin0;
             const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
             const int bx = lb % nbx, by = (lb / nbx) % nby, bz = lb / (nbx * nby);
@@ -301,13 +333,17 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
             }
             const int hs = V.bin_start[gb], hn = V.bin_count[gb];
             const float lo = V.rl2f_lo, hi = V.rl2f_hi;
-
             for (int h0 = 0; h0 < hn; h0 += 32) {
-                const int p = hs + h0 + lane;
-                const bool act = (h0 + lane) < hn;
-                const float4 ri = act ? V.rec[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const uint32_t self_e = ((uint32_t)p << 6) | kSelfCode;
-                int cnt = 0;
+                const int nh = min(32, hn - h0);
+                const int hbase = hs + h0;  // slot of home atom 0 of this chunk
+                __syncwarp();
+                s_h[w][lane] = lane < nh ? V.rec[hbase + lane] : make_float4(-3.0e30f, -3.0e30f, -3.0e30f, 0.f);
+                __syncwarp();
+                // this lane as a home atom: its list
+                const int p = hbase + lane;
+                size_t slot = (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
+                const int jump = (32 << lq) - (tq - 1);
+                int mycnt = 0;
 #pragma unroll 1
                 for (int row = 0; row < 9; ++row) {
                     const int n0 = __shfl_sync(0xffffffffu, my_ct, 3 * row);
@@ -318,52 +354,80 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                     const int s2 = __shfl_sync(0xffffffffu, my_st, 3 * row + 2);
                     const int m = n0 + n1 + n2;
                     const int dy = row % 3 - 1, dz = row / 3 - 1;
+                    const bool self_row = (dy == 0 && dz == 0);
                     const float oy = dy * hy, oz = dz * hz;
                     const uint32_t rcode = ((uint32_t)(dz + 1) << 4) | ((uint32_t)(dy + 1) << 2);
 #pragma unroll 1
                     for (int c0 = 0; c0 < m; c0 += 32) {
+                        // this lane as a candidate, shifted into the home frame
                         const int f = c0 + lane;
-                        float4 st4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
+                        int j = 0, seg = 0;
+                        float qx = 3.0e30f, qy = 3.0e30f, qz = 3.0e30f;
                         if (f < m) {
-                            const int seg = (f >= n0) + (f >= n0 + n1);
-                            const int j = seg == 0 ? s0 + f : (seg == 1 ? s1 + f - n0 : s2 + f - n0 - n1);
+                            seg = (f >= n0) + (f >= n0 + n1);
+                            j = seg == 0 ? s0 + f : (seg == 1 ? s1 + f - n0 : s2 + f - n0 - n1);
                             const float4 rj = V.rec[j];
-                            const int dx = seg - 1;
-                            const uint32_t e = ((uint32_t)j << 6) | (uint32_t)seg | rcode;
-                            st4 = make_float4(rj.x + dx * hx, rj.y + oy, rj.z + oz, __uint_as_float(e));
+                            qx = rj.x + (seg - 1) * hx;
+                            qy = rj.y + oy;
+                            qz = rj.z + oz;
                         }
-                        __syncwarp();
-                        s_c[w][lane] = st4;
-                        __syncwarp();
-                        const int mm = min(32, m - c0);
-#pragma unroll 4
-                        for (int c = 0; c < mm; ++c) {
-                            const float4 q = s_c[w][c];
-                            const float ddx = ri.x - q.x, ddy = ri.y - q.y, ddz = ri.z - q.z;
-                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (!act || r2 >= hi) continue;
-                            const uint32_t e = __float_as_uint(q.w);
-                            if (e == self_e) continue;
-                            if (HALF && entry_j(e) <= p) continue;
-                            bool in = r2 < lo;
-                            if (!in) {
-                                in = in_list_fp64<PREC>(V, R, p, entry_j(e), entry_dx(e), dy, dz);
+                        const uint32_t e = ((uint32_t)j << 6) | (uint32_t)seg | rcode;
+                        // acceptance bits over the home atoms, 8 at a time with
+                        // compile-time bit positions (padding records are far away)
+                        unsigned acc = 0u, acc_hi = 0u;
+#pragma unroll 1
+                        for (int hb = 0; hb < nh; hb += 8) {
+                            unsigned a8 = 0u, b8 = 0u;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float4 ri = s_h[w][hb + k];
+                                const float ddx = ri.x - qx, ddy = ri.y - qy, ddz = ri.z - qz;
+                                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                                if (r2 < lo) a8 |= 1u << k;
+                                if (r2 < hi) b8 |= 1u << k;
                             }
-                            if (in) {
-                                if (cnt < maxn) V.nlist[list_index(p, cnt, lt, lq, maxn)] = e;
-                                ++cnt;
+                            acc |= a8 << hb;
+                            acc_hi |= b8 << hb;
+                        }
+                        unsigned band = acc_hi & ~acc;
+                        // exclusions: the atom itself; for HALF every home atom with slot >= j
+                        const int jh = j - hbase;  // j as a home-atom index, if it is one
+                        if (self_row && seg == 1 && jh >= 0 && jh < 32) {
+                            acc &= ~(1u << jh);
+                            band &= ~(1u << jh);
+                        }
+                        if (HALF) {
+                            const unsigned keep = jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
+                            acc &= keep;
+                            band &= keep;
+                        }
+                        while (band) {  // margin band: decide in FP64 (rare)
+                            const int h = __ffs(band) - 1;
+                            band &= band - 1u;
+                            if (in_list_fp64<PREC>(V, R, hbase + h, j, seg - 1, dy, dz)) acc |= 1u << h;
+                        }
+                        // lane = home atom: bit c set if candidate lane c is accepted
+                        unsigned t = warp_transpose32(acc, lane);
+                        while (__any_sync(0xffffffffu, t != 0u)) {
+                            const int c = t ? __ffs(t) - 1 : lane;
+                            const uint32_t ec = __shfl_sync(0xffffffffu, e, c);
+                            if (t) {
+                                t &= t - 1u;
+                                if (mycnt < maxn) V.nlist[slot] = ec;
+                                ++mycnt;
+                                slot += (mycnt & (tq - 1)) ? 1 : jump;
                             }
                         }
                     }
                 }
-                if (act) {
-                    V.ncount[p] = min(cnt, maxn);
-                    if (cnt > maxn) {
-                        atomicMax(&V.ctl->need_maxneigh, cnt);
+                if (lane < nh) {
+                    V.ncount[p] = min(mycnt, maxn);
+                    if (mycnt > maxn) {
+                        atomicMax(&V.ctl->need_maxneigh, mycnt);
                         latch_error(V.ctl, kErrOverflow);
                     }
-                    my_max = max(my_max, cnt);
-                    my_sum += cnt;
+                    my_max = max(my_max, mycnt);
+                    my_sum += mycnt;
                 }
             }
         }

@@ -477,6 +477,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.key, n);
     AL(V.slot, n);
     AL(V.perm, n);
+    AL(V.sid, n);
     AL(V.bin_count, (size_t)V.nbins_total);
     AL(V.bin_start, (size_t)V.nbins_total + 1);
     AL(V.scan_blk, (size_t)(V.nbins_total + 4095) / 4096 + 1);

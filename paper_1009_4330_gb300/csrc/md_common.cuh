@@ -30,7 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/md.h"
+#include "md.h"  // include/md.h (the C ABI); on the include path
 
 namespace md {
 
@@ -109,7 +109,7 @@ struct View {
     float4 *rec, *recb;   // float(xr) + type; the same at the last build
     // rebuild scratch
     double *tx, *tv;      // [3][n_pad] staged absolute positions / velocities (old order)
-    int *ttype, *tid, *key, *slot, *perm;
+    int *ttype, *tid, *key, *slot, *perm, *sid;
     int *bin_count, *bin_start;
     int *scan_blk;        // per 4096-bin block: exclusive prefix of the bin counts
     int *rep_base;        // per replica: global prefix at its first bin minus its first slot
