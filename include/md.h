@@ -239,6 +239,41 @@ md_status md_info(md_system *h, md_info_t *out);
  */
 md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t cap);
 
+/*
+ * Neighbour lists without allocating anything -- for callers that may not
+ * call cudaMalloc: work issued while a stream is being captured into a CUDA
+ * graph, hosts whose device memory belongs entirely to another allocator (a
+ * framework's caching pool, a fixed arena), latency-critical loops that
+ * cannot afford an allocation.  The paper has no counterpart; this is a
+ * library convenience beside the handle-based path.
+ *
+ * Builds the full Verlet neighbour sets of ONE periodic box: for every atom
+ * i, all j != i with |x_i - x_j|^2 < rl^2 under the minimum image, decided
+ * in FP64 (the same sets as md_get_neighbors after md_build_neighbors with
+ * cutoff + skin = rl).  x: device [n][3] doubles; box: HOST double[3], each
+ * edge >= 2 rl; counts: device int32[n] (true lengths); nbr: device
+ * int32[n][cap], row-major, original indices, unsorted within a row, only
+ * the first min(count, cap) entries of a row written.  Work goes on
+ * `stream` (a cudaStream_t; NULL = legacy default stream) and the call
+ * synchronises it before returning.
+ *
+ * Scratch: one static device array of about 2.6 MB per device that loads the
+ * library, held until the process exits, limiting n to MD_NOALLOC_MAX_ATOMS
+ * and the cell grid to MD_NOALLOC_MAX_BINS cells (coarser cells are used if
+ * needed; results do not change).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress): make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on
+ * the GPU (other threads, other streams) race and must be serialised by the
+ * caller.  Errors: MD_ERR_INVALID (null pointer, n, cap or rl not positive),
+ * MD_ERR_UNSUPPORTED (n > MD_NOALLOC_MAX_ATOMS), MD_ERR_BOX_TOO_SMALL,
+ * MD_ERR_LIST_OVERFLOW (some atom has more than cap neighbours; counts is
+ * still complete), MD_ERR_CUDA; md_last_error(NULL) gives the message.
+ */
+#define MD_NOALLOC_MAX_ATOMS 65536
+#define MD_NOALLOC_MAX_BINS 32768
+md_status md_neighbors_noalloc(int64_t n, const double *x, const double *box, double rl, int32_t *counts,
+                               int32_t *nbr, int32_t cap, void *stream);
+
 /* Synchronise the handle's stream and return (and clear) the latched device status. */
 md_status md_sync_status(md_system *h);
 

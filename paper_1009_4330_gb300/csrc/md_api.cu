@@ -50,6 +50,8 @@ struct md_system {
 
 static thread_local std::string g_err;
 
+void md::set_last_error(const char *msg) { g_err = msg; }
+
 static md_status fail(md_system *h, md_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;

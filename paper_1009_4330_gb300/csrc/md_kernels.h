@@ -44,4 +44,7 @@ cudaError_t launch_backward(const View &V, const double *grad_f, double *grad_x,
 cudaError_t launch_neighbors_out(const View &V, int *counts, int *nbr, int cap, cudaStream_t s);
 int backward_partial_blocks(const View &V);
 
+// set the message md_last_error(NULL) returns (entry points without a handle)
+void set_last_error(const char *msg);
+
 }  // namespace md
