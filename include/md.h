@@ -184,7 +184,7 @@ md_status md_autotune(md_system *h, const char *cache_path);
 /*
  * Select the force-kernel variant directly: tpa (threads per atom) in
  * {1,2,4,8,16,32}, list FULL or HALF, block (threads per block) in
- * {64,128,256}, vec (list entries per thread per load) in {1,4}.  Changing
+ * {64,128,256}, vec (list entries per thread per load) in {1,2,4}.  Changing
  * tpa, list or vec rebuilds the list in the matching layout (and recomputes
  * the forces).
  */

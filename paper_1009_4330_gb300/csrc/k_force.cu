@@ -78,6 +78,26 @@ __device__ __forceinline__ uint4 ld_stream4(const uint32_t *p) {
     return v;
 }
 
+__device__ __forceinline__ uint2 ld_stream2(const uint32_t *p) {
+    uint2 v;
+    asm volatile("ld.global.cs.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
+// this thread's Q list entries of one round, one (vector) load
+template <int Q>
+__device__ __forceinline__ void load_entries(const uint32_t *p, uint32_t (&e)[Q]) {
+    if constexpr (Q == 4) {
+        const uint4 u = ld_stream4(p);
+        e[0] = u.x; e[1] = u.y; e[2] = u.z; e[3] = u.w;
+    } else if constexpr (Q == 2) {
+        const uint2 u = ld_stream2(p);
+        e[0] = u.x; e[1] = u.y;
+    } else {
+        e[0] = ld_stream(p);
+    }
+}
+
 // reduce a double over the T consecutive lanes of a group
 template <int T>
 __device__ __forceinline__ double group_sum(double x) {
@@ -105,24 +125,9 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
     const int nr = (cnt + PER - 1) / PER;
     const real hy4 = hy * (real)0.25, hz16 = hz * (real)0.0625;  // exact: powers of two
     uint32_t cur[Q], nxt[Q];
-    if (nr > 0) {
-        if (Q == 4) {
-            const uint4 u = ld_stream4(lp);
-            cur[0] = u.x; cur[Q > 1 ? 1 : 0] = u.y; cur[Q > 2 ? 2 : 0] = u.z; cur[Q > 3 ? 3 : 0] = u.w;
-        } else {
-            cur[0] = ld_stream(lp);
-        }
-    }
+    if (nr > 0) load_entries<Q>(lp, cur);
     for (int r = 0; r < nr; ++r) {
-        if (r + 1 < nr) {
-            const uint32_t *np = lp + (size_t)(r + 1) * 32 * Q;
-            if (Q == 4) {
-                const uint4 u = ld_stream4(np);
-                nxt[0] = u.x; nxt[Q > 1 ? 1 : 0] = u.y; nxt[Q > 2 ? 2 : 0] = u.z; nxt[Q > 3 ? 3 : 0] = u.w;
-            } else {
-                nxt[0] = ld_stream(np);
-            }
-        }
+        if (r + 1 < nr) load_entries<Q>(lp + (size_t)(r + 1) * 32 * Q, nxt);
         const int left = cnt - (r * PER + sub * Q);
         real xj[Q], yj[Q], zj[Q];
         int tj[Q];
@@ -232,8 +237,15 @@ struct LJPair {
     }
 };
 
+// resident blocks of 256 threads asked of the register allocator: fewer live
+// registers for smaller Q leave room for more warps to hide gather latency
+template <int PREC, int Q, int EV>
+struct LjOcc {
+    static constexpr int value = (PREC == MD_PREC_MIXED && !EV) ? (Q == 4 ? 4 : (Q == 2 ? 5 : 6)) : 1;
+};
+
 template <int PREC, int T, int Q, int HALF, int EV, int MT>
-__global__ void __launch_bounds__(256, (PREC == MD_PREC_MIXED && !EV) ? 4 : 1) k_lj(View V, KArgs a) {
+__global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
     __shared__ real s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
@@ -616,7 +628,9 @@ static const void *pick_lj_q(int T, int half, int ev, int mt) {
 
 template <int PREC>
 static const void *pick_lj_prec(int T, int Q, int half, int ev, int mt) {
-    return Q == 4 ? pick_lj_q<PREC, 4>(T, half, ev, mt) : pick_lj_q<PREC, 1>(T, half, ev, mt);
+    if (Q == 4) return pick_lj_q<PREC, 4>(T, half, ev, mt);
+    if (Q == 2) return pick_lj_q<PREC, 2>(T, half, ev, mt);
+    return pick_lj_q<PREC, 1>(T, half, ev, mt);
 }
 
 template <int PREC, int Q>
@@ -633,7 +647,9 @@ static const void *pick_rho_q(int T) {
 
 template <int PREC>
 static const void *pick_rho(int T, int Q) {
-    return Q == 4 ? pick_rho_q<PREC, 4>(T) : pick_rho_q<PREC, 1>(T);
+    if (Q == 4) return pick_rho_q<PREC, 4>(T);
+    if (Q == 2) return pick_rho_q<PREC, 2>(T);
+    return pick_rho_q<PREC, 1>(T);
 }
 
 template <int PREC, int Q, int EV>
@@ -651,6 +667,7 @@ static const void *pick_eamf_q(int T) {
 template <int PREC>
 static const void *pick_eamf(int T, int Q, int ev) {
     if (Q == 4) return ev ? pick_eamf_q<PREC, 4, 1>(T) : pick_eamf_q<PREC, 4, 0>(T);
+    if (Q == 2) return ev ? pick_eamf_q<PREC, 2, 1>(T) : pick_eamf_q<PREC, 2, 0>(T);
     return ev ? pick_eamf_q<PREC, 1, 1>(T) : pick_eamf_q<PREC, 1, 0>(T);
 }
 
@@ -680,8 +697,8 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
     } else {
         KArgs ar = a;
         ar.in_graph = 0;
-        seq.push_back(KCall{fp64 ? pick_rho<MD_PREC_FP64>(T, V.vec) : pick_rho<MD_PREC_MIXED>(T, V.vec), grid,
-                            dim3(block), 0, ar});
+        const void *fr = fp64 ? pick_rho<MD_PREC_FP64>(T, V.vec) : pick_rho<MD_PREC_MIXED>(T, V.vec);
+        seq.push_back(KCall{fr, grid, dim3(block), 0, ar});
         const void *fn = fp64 ? pick_eamf<MD_PREC_FP64>(T, V.vec, ev) : pick_eamf<MD_PREC_MIXED>(T, V.vec, ev);
         seq.push_back(KCall{fn, grid, dim3(block), 0, a});
     }

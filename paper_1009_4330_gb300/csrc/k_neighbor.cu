@@ -95,7 +95,7 @@ __global__ void k_prepare(View V, KArgs a) {
     }
     for (int c = 0; c < 3; ++c) V.tx[c * n + p] = xr[c];
     if (!finite) latch_error(V.ctl, kErrNonfinite);
-    const int gb = R.bin0 + (bc[2] * R.nb[1] + bc[1]) * R.nb[0] + bc[0];
+    const int gb = V.lin2bin[R.bin0 + (bc[2] * R.nb[1] + bc[1]) * R.nb[0] + bc[0]];
     V.key[p] = gb;
     // atoms of a warp are mostly in one or two bins: one atomic per distinct
     // bin, each lane taking its rank among the lanes of its bin
@@ -109,6 +109,11 @@ __global__ void k_prepare(View V, KArgs a) {
     base = __shfl_sync(same, base, leader);
     V.slot[p] = base + rank;
 }
+
+// Bins of a replica are numbered along a Morton (Z-order) curve through its
+// cell grid, so that atoms consecutive in memory -- those of one warp, one
+// block, one SM -- fill compact 3-D regions whose neighbours overlap: the
+// gathers of the force loop then hit L1 more often.
 
 // bin_start[b] = first slot of bin b: an exclusive scan of the bin counts,
 // segmented per replica (each replica's slots start at its atom0), in three
@@ -230,8 +235,8 @@ __global__ void k_gather(View V, KArgs a) {
     int rank = 0;
     for (int k = 0; k < cnt; ++k) rank += (V.sid[s + k] < myid);
     const int dst = s + rank;
-    const int lb = gb - R.bin0;
-    const int bc[3] = {lb % R.nb[0], (lb / R.nb[0]) % R.nb[1], lb / (R.nb[0] * R.nb[1])};
+    const int xyz = V.bin2xyz[gb];
+    const int bc[3] = {unpack_bx(xyz), unpack_by(xyz), unpack_bz(xyz)};
     double xr[3];
     for (int c = 0; c < 3; ++c) {
         xr[c] = V.tx[c * n + src];
@@ -314,9 +319,9 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
             const Rep &R = V.rep[r];
             const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
             const int la = 5 - lt, ltq = lt + lq, tq = 1 << ltq;
-            const int lb = gb - R.bin0;
             const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
-            const int bx = lb % nbx, by = (lb / nbx) % nby, bz = lb / (nbx * nby);
+            const int xyz = V.bin2xyz[gb];
+            const int bx = unpack_bx(xyz), by = unpack_by(xyz), bz = unpack_bz(xyz);
             const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
             // neighbour cell (row = lane / 3, dx = lane % 3 - 1) bounds, one lane each
             int my_st = 0, my_ct = 0;
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                 cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
                 cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
                 cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
-                const int nbin = R.bin0 + (cz * nby + cy) * nbx + cx;
+                const int nbin = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
                 my_st = V.bin_start[nbin];
                 my_ct = V.bin_count[nbin];
             }

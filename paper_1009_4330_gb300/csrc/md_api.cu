@@ -459,9 +459,13 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.rep_flag, (size_t)n_rep);
     AL(V.rep_maxcnt, (size_t)n_rep);
     AL(V.rep_entries, (size_t)n_rep);
-    int *d_bin_rep;
+    int *d_bin_rep, *d_lin2bin, *d_bin2xyz;
     AL(d_bin_rep, (size_t)V.nbins_total);
+    AL(d_lin2bin, (size_t)V.nbins_total);
+    AL(d_bin2xyz, (size_t)V.nbins_total);
     V.bin_rep = d_bin_rep;
+    V.lin2bin = d_lin2bin;
+    V.bin2xyz = d_bin2xyz;
     AL(V.ev_tile, (size_t)V.n_tiles * 8);
     if (V.prec == MD_PREC_FP64) AL(V.pos4, n);
     else AL(V.xr, 3 * n);
@@ -500,10 +504,32 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
         md_status st = alloc_list(h, initial_maxneigh(h->reps, rl));
         if (st) { md_destroy(h); return st; }
     }
-    std::vector<int> tile_rep(V.n_tiles), bin_rep(V.nbins_total);
+    std::vector<int> tile_rep(V.n_tiles), bin_rep(V.nbins_total), lin2bin(V.nbins_total), bin2xyz(V.nbins_total);
     for (int r = 0; r < n_rep; ++r) {
-        for (int t = 0; t < h->reps[r].ntiles; ++t) tile_rep[h->reps[r].tile0 + t] = r;
-        for (int b = 0; b < h->reps[r].nbins; ++b) bin_rep[h->reps[r].bin0 + b] = r;
+        const Rep &R = h->reps[r];
+        for (int t = 0; t < R.ntiles; ++t) tile_rep[R.tile0 + t] = r;
+        for (int b = 0; b < R.nbins; ++b) bin_rep[R.bin0 + b] = r;
+        // Morton rank of every cell: sort the cells by their interleaved coordinates
+        std::vector<std::pair<uint64_t, int>> order((size_t)R.nbins);
+        for (int bz = 0; bz < R.nb[2]; ++bz)
+            for (int by = 0; by < R.nb[1]; ++by)
+                for (int bx = 0; bx < R.nb[0]; ++bx) {
+                    uint64_t code = 0;
+                    for (int bit = 0; bit < 10; ++bit) {
+                        code |= (uint64_t)((bx >> bit) & 1) << (3 * bit);
+                        code |= (uint64_t)((by >> bit) & 1) << (3 * bit + 1);
+                        code |= (uint64_t)((bz >> bit) & 1) << (3 * bit + 2);
+                    }
+                    const int lin = (bz * R.nb[1] + by) * R.nb[0] + bx;
+                    order[(size_t)lin] = {code, lin};
+                }
+        std::sort(order.begin(), order.end());
+        for (int rank = 0; rank < R.nbins; ++rank) {
+            const int lin = order[(size_t)rank].second;
+            const int bx = lin % R.nb[0], by = (lin / R.nb[0]) % R.nb[1], bz = lin / (R.nb[0] * R.nb[1]);
+            lin2bin[R.bin0 + lin] = R.bin0 + rank;
+            bin2xyz[R.bin0 + rank] = bx | (by << 10) | (bz << 20);
+        }
     }
     // validate types on the host (one copy at creation)
     for (int r = 0; r < n_rep; ++r) {
@@ -530,6 +556,8 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     CKD(cudaMemcpyAsync(d_rep, h->reps.data(), sizeof(Rep) * n_rep, cudaMemcpyHostToDevice, h->s));
     CKD(cudaMemcpyAsync(d_tile_rep, tile_rep.data(), sizeof(int) * V.n_tiles, cudaMemcpyHostToDevice, h->s));
     CKD(cudaMemcpyAsync(d_bin_rep, bin_rep.data(), sizeof(int) * V.nbins_total, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemcpyAsync(d_lin2bin, lin2bin.data(), sizeof(int) * V.nbins_total, cudaMemcpyHostToDevice, h->s));
+    CKD(cudaMemcpyAsync(d_bin2xyz, bin2xyz.data(), sizeof(int) * V.nbins_total, cudaMemcpyHostToDevice, h->s));
     CKD(cudaMemsetAsync(V.rep_maxcnt, 0, sizeof(int) * n_rep, h->s));
     CKD(cudaMemsetAsync(V.rep_entries, 0, sizeof(unsigned long long) * n_rep, h->s));
     CKD(cudaMemsetAsync(V.rep_disp, 0, sizeof(unsigned) * n_rep, h->s));
@@ -739,7 +767,7 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
     if (list == MD_LIST_HALF && h->cfg.pot != MD_POT_LJ)
         return fail(h, MD_ERR_UNSUPPORTED, "half lists are implemented for LJ only");
     if (block != 64 && block != 128 && block != 256) return fail(h, MD_ERR_INVALID, "block must be 64, 128 or 256");
-    if (vec != 1 && vec != 4) return fail(h, MD_ERR_INVALID, "vec must be 1 or 4");
+    if (vec != 1 && vec != 2 && vec != 4) return fail(h, MD_ERR_INVALID, "vec must be 1, 2 or 4");
     const int half = list == MD_LIST_HALF ? 1 : 0;
     const bool relayout = (tpa != h->V.tpa) || (half != h->V.half) || (vec != h->V.vec);
     h->V.tpa = tpa;
@@ -785,7 +813,7 @@ md_status md_autotune(md_system *h, const char *cache_path) {
     int bt = 1, bl = MD_LIST_FULL, bb = 256, bq = 1;
     for (int l : lists)
         for (int t : {1, 2, 4, 8, 16, 32})
-            for (int q : {1, 4})
+            for (int q : {1, 2, 4})
             for (int b : {128, 256}) {
                 st = md_set_kernel(h, t, (md_listkind)l, b, q);
                 if (st) {

@@ -19,7 +19,7 @@
 //     codes sit in the low bits so that each decodes to an exact float with
 //     one mask-or and one add (see code_x/y/z);
 //   * list order is tiled for a thread group of T threads per atom, each
-//     thread loading Q consecutive entries at once (Q = 1 or 4): with
+//     thread loading Q consecutive entries at once (Q = 1, 2 or 4): with
 //     A = 32 / T atoms per warp, entry k of atom i sits at
 //         (i / A) * A * maxneigh + (k / (T Q)) * 32 Q + ((i % A) T + (k / Q) % T) Q + k % Q,
 //     so every warp-wide list load is one contiguous 128 Q-byte block and a
@@ -86,7 +86,7 @@ struct PairTab {
 struct View {
     int n_pad, n_tiles, n_rep, nbins_total, maxneigh;
     int tpa;          // threads per atom the list is laid out for
-    int vec;          // entries per thread per list load (1 or 4)
+    int vec;          // entries per thread per list load (1, 2 or 4)
     int ltpa, lvec;   // log2 of tpa and vec
     int half;         // 1: half list (each pair once, Newton-3 atomics)
     int prec;         // md_precision
@@ -97,6 +97,8 @@ struct View {
     const Rep *rep;
     const int *tile_rep;
     const int *bin_rep;   // replica of each global bin
+    const int *lin2bin;   // per replica, cell (bz nby + by) nbx + bx -> global bin (Morton-curve rank)
+    const int *bin2xyz;   // global bin -> packed cell coordinates
     unsigned *rep_disp;   // per replica: max |x - x_build|^2 since the build, as float bits
     int *rep_flag;        // per replica: 1 = rebuild in this step
     int *rep_maxcnt;      // per replica: longest list at its last build
