@@ -257,6 +257,14 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# DRAM traffic of the force kernel per atom, from the ncu capture summarised in
+# profiles/k_lj_lj500k_mixed_full.md (dram__bytes_read.sum + dram__bytes_write.sum
+# = 174.3 MB for 500,000 atoms; scaled by atoms, the list length per atom being
+# the same).  Valid for that variant only: T = 1 thread per atom, Q = 4, full list.
+K_LJ_TRAFFIC_PER_ATOM = 174.3e6 / 500000
+K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -292,6 +300,8 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = load_peaks()
     achieved = f_bytes / (f_ms / 1000.0) / 1e9
     info = s.info()
+    same_variant = all(info[k] == v for k, v in K_LJ_TRAFFIC_VARIANT.items())
+    traffic = K_LJ_TRAFFIC_PER_ATOM * n if same_variant else None
     e2e = e2e_run(s, d, K)
     extras = {}
     if not args.no_extras and rank == 0:
@@ -310,7 +320,8 @@ def run_ours(args, ws, rank, local):
                        "steps_per_rebuild": (K / rebuilds) if rebuilds else None,
                        "l2": "working set > L2 (list alone ~0.3 GB): no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_lj (force + kick, md_step form)", "peak_kind": peak_kind,
+                         "traffic": traffic, "traffic_source": "profiles/k_lj_lj500k_mixed_full.md (scaled by atoms)",
+                         "kernel": "k_lj (force + kick, md_step form)", "peak_kind": peak_kind,
                          "force_ms": f_ms, "force_algorithmic_bytes": f_bytes,
                          "force_share_of_step": f_ms / (ms / K)},
             "clocks": clocks,
@@ -354,6 +365,15 @@ def side_runs(synth, cells, K, W):
     out["eam500000_mixed"] = {"value": e["x"].shape[0] * k / (ms / 1000), "steps": k, "tpa": i1["tpa"],
                               "force_GBs": fby / (fms / 1000) / 1e9}
     s.close()
+    # 4,000-atom LJ liquid, plain FP64, 100 steps (latency-bound small system)
+    c0 = synth.config0()
+    s = System.lj(c0["x"], c0["v"], c0["box"], cutoff=2.5, skin=0.3, dt=0.005, mass=1.0, precision="fp64", tpa=0)
+    ms, i0, i1, _ = time_steps(s, 100, 10)
+    out["fp64_lj4000_100steps"] = {"value": 4000 * 100 / (ms / 1000), "ms_per_step": ms / 100, "tpa": i1["tpa"],
+                                   "list": i1["list"]}
+    s.close()
+    # force matching: forward forces + backward (positions and 6 parameters), 32,768 atoms
+    out["force_matching_32768"] = force_matching_timing(synth)
     # batched replicas (512, log-uniform 500..20000), mixed
     b = synth.config4()
     s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
@@ -366,6 +386,39 @@ def side_runs(synth, cells, K, W):
                              "force_GBs": fby / (fms / 1000) / 1e9}
     s.close()
     torch.cuda.synchronize()
+    return out
+
+
+def force_matching_timing(synth, reps=20):
+    """Time per forward (forces) + backward (dL/dx, dL/d(eps, sigma)) of the
+    32,768-atom binary LJ force-matching workload, CUDA events."""
+    import torch
+    from paper_1009_4330_gb300 import System
+    c = synth.config3()
+    v = np.zeros_like(c["x"])
+    e0, s0 = synth.pair_matrix(c["eps0"]), synth.pair_matrix(c["sig0"])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = System.lj(c["x"], v, c["box"], eps=e0, sig=s0, types=c["types"], n_types=2, cutoff=2.5, skin=0.3,
+                      dt=0.005, mass=[1.0, 1.0], precision=prec, tpa=0)
+        g = torch.ones((c["x"].shape[0], 3), dtype=torch.float64, device="cuda")
+        f = torch.empty_like(g)
+        for _ in range(3):
+            s.compute_forces(out=f)
+            s.backward(g)
+        torch.cuda.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record()
+        for _ in range(reps):
+            s.compute_forces(out=f)
+            s.backward(g)
+        e1_.record()
+        torch.cuda.synchronize()
+        ms = e0_.elapsed_time(e1_) / reps
+        info = s.info()
+        out[prec] = {"ms_per_fwd_bwd": ms, "pair_evaluations_per_s": 2 * info["list_entries"] / (ms / 1000),
+                     "tpa": info["tpa"]}
+        s.close()
     return out
 
 

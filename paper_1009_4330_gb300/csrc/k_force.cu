@@ -59,8 +59,10 @@ struct Pol<MD_PREC_FP64> {
         x = q.x; y = q.y; z = q.z; t = (int)__double_as_longlong(q.w);
     }
     __device__ static __forceinline__ double h(const Rep &R, int c) { return R.h[c]; }
-    __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
-    __device__ static __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+    // FP64 throughput is low on this GPU: Newton iterations from the FP32
+    // approximations instead of a full-precision divide / square root
+    __device__ static __forceinline__ double rcp(double x) { return rcp_newton(x); }
+    __device__ static __forceinline__ double rsqrt(double x) { return rsqrt_newton(x); }
     __device__ static __forceinline__ double fp(const View &V, int j) { return V.fp64[j]; }
 };
 
@@ -507,64 +509,82 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
 // x += dt v (after v += dt/2 a(F) on the first step of an md_step call);
 // refresh the FP32 record; per-replica max displacement since the build;
 // the last block turns it into per-replica rebuild flags and sets the
-// rebuild conditional of the step graph.
+// rebuild conditional of the step graph.  One atom per thread (two per
+// thread measured slower: fewer loads in flight per SM).
+constexpr int kDriftPer = 1;
+
 template <int PREC>
-__global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
-    __shared__ double s_ftm[kMaxTypes];
-    __shared__ float s_m[32];
-    __shared__ int s_r[32];
-    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
-    __syncthreads();
-    const unsigned err = V.ctl->err;
-    const int first = V.ctl->first;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ float drift_one(const View &V, int p, int first, int &rep) {
     const int n = V.n_pad;
-    float d2 = 0.f;
-    int r = -1;
-    if (p < n) {
-        r = V.tile_rep[p >> 5];
-        const Rep &R = V.rep[r];
-        if (err == 0 && (p - R.atom0) < R.natoms) {
-            double x[3], v[3];
-            int t;
-            if (PREC == MD_PREC_FP64) {
-                const double4_32a q = V.pos4[p];
-                x[0] = q.x; x[1] = q.y; x[2] = q.z;
-                t = (int)__double_as_longlong(q.w);
-            } else {
-                for (int c = 0; c < 3; ++c) x[c] = V.xr[c * n + p];
-                t = V.type[p];
-            }
-            for (int c = 0; c < 3; ++c) v[c] = V.v[c * n + p];
-            if (first) {
-                const double hk = 0.5 * V.dt * s_ftm[t];
-                for (int c = 0; c < 3; ++c) {
-                    v[c] += hk * V.f[c * n + p];
-                    V.v[c * n + p] = v[c];
-                }
-            }
-            for (int c = 0; c < 3; ++c) x[c] += V.dt * v[c];
-            const float4 nr = make_float4((float)x[0], (float)x[1], (float)x[2], __int_as_float(t));
-            if (PREC == MD_PREC_FP64) {
-                V.pos4[p] = make_double4_32a(x[0], x[1], x[2], __longlong_as_double((long long)t));
-            } else {
-                for (int c = 0; c < 3; ++c) V.xr[c * n + p] = x[c];
-                V.rec[p] = nr;
-            }
-            const float4 b = V.recb[p];
-            const float ex = nr.x - b.x, ey = nr.y - b.y, ez = nr.z - b.z;
-            d2 = ex * ex + ey * ey + ez * ez;
-            if (!(d2 <= 3.0e38f)) d2 = __int_as_float(0x7f800000);  // NaN/Inf -> +Inf
+    rep = V.tile_rep[p >> 5];
+    const Rep &R = V.rep[rep];
+    if ((p - R.atom0) >= R.natoms) return 0.f;
+    double x[3], v[3];
+    int t;
+    if (PREC == MD_PREC_FP64) {
+        const double4_32a q = V.pos4[p];
+        x[0] = q.x; x[1] = q.y; x[2] = q.z;
+        t = (int)__double_as_longlong(q.w);
+    } else {
+        for (int c = 0; c < 3; ++c) x[c] = V.xr[c * n + p];
+        t = V.type[p];
+    }
+    for (int c = 0; c < 3; ++c) v[c] = V.v[c * n + p];
+    const float4 b = V.recb[p];
+    if (first) {
+        const double hk = 0.5 * V.dt * V.tab->ftm_m[t];
+        for (int c = 0; c < 3; ++c) {
+            v[c] += hk * V.f[c * n + p];
+            V.v[c * n + p] = v[c];
         }
     }
-    const float wm = warp_max(d2);
+    for (int c = 0; c < 3; ++c) x[c] += V.dt * v[c];
+    const float4 nr = make_float4((float)x[0], (float)x[1], (float)x[2], __int_as_float(t));
+    if (PREC == MD_PREC_FP64) {
+        V.pos4[p] = make_double4_32a(x[0], x[1], x[2], __longlong_as_double((long long)t));
+    } else {
+        for (int c = 0; c < 3; ++c) V.xr[c * n + p] = x[c];
+        V.rec[p] = nr;
+    }
+    const float ex = nr.x - b.x, ey = nr.y - b.y, ez = nr.z - b.z;
+    float d2 = ex * ex + ey * ey + ez * ez;
+    if (!(d2 <= 3.0e38f)) d2 = __int_as_float(0x7f800000);  // NaN/Inf -> +Inf
+    return d2;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
+    __shared__ float s_m[kDriftPer * 8];
+    __shared__ int s_r[kDriftPer * 8];
+    const unsigned err = V.ctl->err;
+    const int first = V.ctl->first;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { s_m[w] = wm; s_r[w] = r; }
+    const int p0 = blockIdx.x * (256 * kDriftPer) + threadIdx.x;
+    float d2[kDriftPer];
+    int rep[kDriftPer];
+#pragma unroll
+    for (int u = 0; u < kDriftPer; ++u) {
+        const int p = p0 + u * 256;
+        d2[u] = 0.f;
+        rep[u] = -1;
+        if (p < V.n_pad) {
+            if (err == 0) {
+                d2[u] = drift_one<PREC>(V, p, first, rep[u]);
+            } else {
+                rep[u] = V.tile_rep[p >> 5];  // a latched error: leave the state as it is
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kDriftPer; ++u) {
+        const float wm = warp_max(d2[u]);
+        if (lane == 0) { s_m[u * 8 + w] = wm; s_r[u * 8 + w] = rep[u]; }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // merge runs of warps of the same replica, one atomic per run
         int cr = -1;
         float cm = 0.f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        for (int k = 0; k < kDriftPer * (int)(blockDim.x >> 5); ++k) {
             if (s_r[k] != cr) {
                 if (cr >= 0 && cm > 0.f) atomicMax(&V.rep_disp[cr], __float_as_uint(cm));
                 cr = s_r[k];
@@ -709,7 +729,7 @@ void drift_sequence(const View &V, bool in_graph, std::vector<KCall> &seq) {
     a.in_graph = in_graph ? 1 : 0;
     seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_drift<MD_PREC_FP64>
                                                : (const void *)k_drift<MD_PREC_MIXED>,
-                        dim3((V.n_pad + 255) / 256), dim3(256), 0, a});
+                        dim3((V.n_pad + 256 * kDriftPer - 1) / (256 * kDriftPer)), dim3(256), 0, a});
 }
 
 void loop_init_sequence(const View &V, std::vector<KCall> &seq) {

@@ -150,12 +150,21 @@ template <int PREC, int T, int NTM>
 __global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
     constexpr int NQ = NTM * NTM;
     __shared__ double s_red[8][2 * NQ];
+    __shared__ double s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
+    __shared__ double s_ie[kMaxTypes * kMaxTypes], s_is[kMaxTypes * kMaxTypes];
+    const int nt = V.ntypes;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
+        s_lj1[k] = V.tab->lj1[k];
+        s_lj2[k] = V.tab->lj2[k];
+        s_ie[k] = V.tab->inv_eps[k];
+        s_is[k] = V.tab->inv_sig[k];
+    }
+    __syncthreads();
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int p = gw * A + lane / T;
     const int sub = lane & (T - 1);
-    const int nt = V.ntypes;
     const int n = V.n_pad;
     double ge[NQ], gsg[NQ];
     for (int q = 0; q < NQ; ++q) { ge[q] = 0.0; gsg[q] = 0.0; }
@@ -170,37 +179,36 @@ __global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
             int ti;
             load64<PREC>(V, p, xi, yi, zi, ti);
             const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
-            const int maxn = V.maxneigh;
-            const int Q = V.vec;
-            for (int k = 0; k < cnt; ++k) {
-                // this thread's share of the list layout: entries r T Q + sub Q + q
-                if ((k / Q) % T != sub) continue;
-                const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, maxn)];
-                const int j = entry_j(e);
-                double xj, yj, zj;
-                int tj;
-                load64<PREC>(V, j, xj, yj, zj, tj);
-                const double dx = xi - xj - entry_dx(e) * R.h[0];
-                const double dy = yi - yj - entry_dy(e) * R.h[1];
-                const double dz = zi - zj - entry_dz(e) * R.h[2];
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (!(r2 < V.rc2)) continue;
-                const int tp = ti * nt + tj;
-                const double lj1 = V.tab->lj1[tp], lj2 = V.tab->lj2[tp];
-                const double r2i = 1.0 / r2, r6i = r2i * r2i * r2i;
-                const double s = r6i * (lj1 * r6i - lj2) * r2i;
-                const double spr = r6i * r2i * r2i * (-14.0 * lj1 * r6i + 8.0 * lj2);
-                const double dgx = gix - V.gs[j], dgy = giy - V.gs[n + j], dgz = giz - V.gs[2 * n + j];
-                const double ddg = dx * dgx + dy * dgy + dz * dgz;
-                gx += s * dgx + spr * dx * ddg;
-                gy += s * dgy + spr * dy * ddg;
-                gz += s * dgz + spr * dz * ddg;
-                const double gd = gix * dx + giy * dy + giz * dz;
-                const int ta = min(ti, tj), tb = max(ti, tj);
-                const int q = (NTM == 1) ? 0 : ta * NTM + tb;
-                const double sg = V.tab->sig[tp];
-                ge[q] += gd * s / V.tab->eps[tp];
-                gsg[q] += gd * (r2i * r6i / sg) * (12.0 * lj1 * r6i - 6.0 * lj2);
+            const int maxn = V.maxneigh, Q = V.vec;
+            // this thread's share of the list layout: entries r T Q + sub Q + q
+            for (int k0 = sub * Q; k0 < cnt; k0 += T * Q) {
+                for (int k = k0; k < k0 + Q && k < cnt; ++k) {
+                    const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, maxn)];
+                    const int j = entry_j(e);
+                    double xj, yj, zj;
+                    int tj;
+                    load64<PREC>(V, j, xj, yj, zj, tj);
+                    const double dx = xi - xj - entry_dx(e) * R.h[0];
+                    const double dy = yi - yj - entry_dy(e) * R.h[1];
+                    const double dz = zi - zj - entry_dz(e) * R.h[2];
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (!(r2 < V.rc2)) continue;
+                    const int tp = ti * nt + tj;
+                    const double lj1 = s_lj1[tp], lj2 = s_lj2[tp];
+                    const double r2i = rcp_newton(r2), r6i = r2i * r2i * r2i;
+                    const double s = r6i * (lj1 * r6i - lj2) * r2i;
+                    const double spr = r6i * r2i * r2i * (-14.0 * lj1 * r6i + 8.0 * lj2);
+                    const double dgx = gix - V.gs[j], dgy = giy - V.gs[n + j], dgz = giz - V.gs[2 * n + j];
+                    const double ddg = dx * dgx + dy * dgy + dz * dgz;
+                    gx += s * dgx + spr * dx * ddg;
+                    gy += s * dgy + spr * dy * ddg;
+                    gz += s * dgz + spr * dz * ddg;
+                    const double gd = gix * dx + giy * dy + giz * dz;
+                    const int ta = min(ti, tj), tb = max(ti, tj);
+                    const int q = (NTM == 1) ? 0 : ta * NTM + tb;
+                    ge[q] += gd * s * s_ie[tp];
+                    gsg[q] += gd * (r2i * r6i * s_is[tp]) * (12.0 * lj1 * r6i - 6.0 * lj2);
+                }
             }
         }
     }

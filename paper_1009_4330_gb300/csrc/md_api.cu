@@ -280,6 +280,8 @@ static void fill_tab(md_system *h, PairTab &t) {
                 const double s6 = std::pow(s, 6.0), s12 = s6 * s6;
                 t.eps[p] = e;
                 t.sig[p] = s;
+                t.inv_eps[p] = e != 0.0 ? 1.0 / e : 0.0;
+                t.inv_sig[p] = s != 0.0 ? 1.0 / s : 0.0;
                 t.lj1[p] = 48.0 * e * s12;
                 t.lj2[p] = 24.0 * e * s6;
                 t.lj3[p] = 4.0 * e * s12;

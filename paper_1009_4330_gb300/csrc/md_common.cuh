@@ -74,6 +74,7 @@ struct PairTab {
     double lj1[kMaxTypes * kMaxTypes], lj2[kMaxTypes * kMaxTypes];
     double lj3[kMaxTypes * kMaxTypes], lj4[kMaxTypes * kMaxTypes], off[kMaxTypes * kMaxTypes];
     double eps[kMaxTypes * kMaxTypes], sig[kMaxTypes * kMaxTypes];
+    double inv_eps[kMaxTypes * kMaxTypes], inv_sig[kMaxTypes * kMaxTypes];
     float lj1f[kMaxTypes * kMaxTypes], lj2f[kMaxTypes * kMaxTypes];
     float lj3f[kMaxTypes * kMaxTypes], lj4f[kMaxTypes * kMaxTypes], offf[kMaxTypes * kMaxTypes];
     double ftm_m[kMaxTypes];  // ftm2v / mass
@@ -199,6 +200,33 @@ __device__ __forceinline__ float code_x(uint32_t e) { return __int_as_float(0x4B
 __device__ __forceinline__ float code_y4(uint32_t e) { return __int_as_float(0x4B400000u | (e & 0xCu)) - 12582916.0f; }
 __device__ __forceinline__ float code_z16(uint32_t e) {
     return __int_as_float(0x4B400000u | (e & 0x30u)) - 12582928.0f;
+}
+
+// FP64 reciprocal by Newton-Raphson (y <- y (2 - x y), quadratic convergence)
+// from the FP32 hardware approximation (relative error < 2^-22): three steps
+// reach double precision.  For 0 < x < FLT_MAX (squared distances here).
+__device__ __forceinline__ double rcp_newton(double x) {
+    float xf = (float)x, yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+    double y = (double)yf;
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// FP64 reciprocal square root by Newton-Raphson (y <- y (3 - x y^2) / 2)
+// from the FP32 hardware approximation: three steps reach double precision.
+// For FLT_MIN < x < FLT_MAX.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    float xf = (float)x, yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+    double y = (double)yf;
+    const double hx = 0.5 * x;
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    return y;
 }
 
 __device__ __forceinline__ float warp_max(float x) {
