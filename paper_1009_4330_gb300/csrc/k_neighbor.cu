@@ -337,12 +337,18 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                 my_ct = V.bin_count[nbin];
             }
             const int hs = V.bin_start[gb], hn = V.bin_count[gb];
-            const float lo = V.rl2f_lo, hi = V.rl2f_hi;
+            const float rl2f = 0.5f * (V.rl2f_lo + V.rl2f_hi), margin = 0.5f * (V.rl2f_hi - V.rl2f_lo);
             for (int h0 = 0; h0 < hn; h0 += 32) {
                 const int nh = min(32, hn - h0);
                 const int hbase = hs + h0;  // slot of home atom 0 of this chunk
                 __syncwarp();
-                s_h[w][lane] = lane < nh ? V.rec[hbase + lane] : make_float4(-3.0e30f, -3.0e30f, -3.0e30f, 0.f);
+                {
+                    // home record with |r|^2 in .w; padding far away (never accepted, never in the band)
+                    float4 hr = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
+                    if (lane < nh) hr = V.rec[hbase + lane];
+                    hr.w = hr.x * hr.x + hr.y * hr.y + hr.z * hr.z;
+                    s_h[w][lane] = hr;
+                }
                 __syncwarp();
                 // this lane as a home atom: its list
                 const int p = hbase + lane;
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                         // this lane as a candidate, shifted into the home frame
                         const int f = c0 + lane;
                         int j = 0, seg = 0;
-                        float qx = 3.0e30f, qy = 3.0e30f, qz = 3.0e30f;
+                        float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
                         if (f < m) {
                             seg = (f >= n0) + (f >= n0 + n1);
                             j = seg == 0 ? s0 + f : (seg == 1 ? s1 + f - n0 : s2 + f - n0 - n1);
@@ -378,39 +384,40 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                         }
                         const uint32_t e = ((uint32_t)j << 6) | (uint32_t)seg | rcode;
                         // acceptance bits over the home atoms, 8 at a time with
-                        // compile-time bit positions (padding records are far away)
-                        unsigned acc = 0u, acc_hi = 0u;
+                        // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
+                        // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
+                        // < ~1e-5 rl^2 here, far inside the margin); the sign bit of t
+                        // is the decision, and the smallest |t| flags the margin band.
+                        const float qx2 = -2.0f * qx, qy2 = -2.0f * qy, qz2 = -2.0f * qz;
+                        const float q2m = qx * qx + qy * qy + qz * qz - rl2f;
+                        unsigned acc = 0u;
+                        float tmin = 3.0e38f;
 #pragma unroll 1
                         for (int hb = 0; hb < nh; hb += 8) {
-                            unsigned a8 = 0u, b8 = 0u;
+                            unsigned a8 = 0u;
 #pragma unroll
                             for (int k = 0; k < 8; ++k) {
                                 const float4 ri = s_h[w][hb + k];
-                                const float ddx = ri.x - qx, ddy = ri.y - qy, ddz = ri.z - qz;
-                                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                                if (r2 < lo) a8 |= 1u << k;
-                                if (r2 < hi) b8 |= 1u << k;
+                                const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                                a8 |= (__float_as_uint(t) >> 31) << k;
+                                tmin = fminf(tmin, fabsf(t));
                             }
                             acc |= a8 << hb;
-                            acc_hi |= b8 << hb;
                         }
-                        unsigned band = acc_hi & ~acc;
+                        if (tmin < margin) {  // margin band: decide those pairs in FP64 (rare)
+                            for (int h = 0; h < nh; ++h) {
+                                const float4 ri = s_h[w][h];
+                                const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                                if (fabsf(t) < margin) {
+                                    const bool in = in_list_fp64<PREC>(V, R, hbase + h, j, seg - 1, dy, dz);
+                                    acc = in ? (acc | (1u << h)) : (acc & ~(1u << h));
+                                }
+                            }
+                        }
                         // exclusions: the atom itself; for HALF every home atom with slot >= j
                         const int jh = j - hbase;  // j as a home-atom index, if it is one
-                        if (self_row && seg == 1 && jh >= 0 && jh < 32) {
-                            acc &= ~(1u << jh);
-                            band &= ~(1u << jh);
-                        }
-                        if (HALF) {
-                            const unsigned keep = jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
-                            acc &= keep;
-                            band &= keep;
-                        }
-                        while (band) {  // margin band: decide in FP64 (rare)
-                            const int h = __ffs(band) - 1;
-                            band &= band - 1u;
-                            if (in_list_fp64<PREC>(V, R, hbase + h, j, seg - 1, dy, dz)) acc |= 1u << h;
-                        }
+                        if (self_row && seg == 1 && jh >= 0 && jh < 32) acc &= ~(1u << jh);
+                        if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
                         // lane = home atom: bit c set if candidate lane c is accepted
                         unsigned t = warp_transpose32(acc, lane);
                         while (__any_sync(0xffffffffu, t != 0u)) {
