@@ -411,8 +411,14 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
         const double Aemb = V.tab->eam[1];
         const double sr = sqrt(rho);
         const double fpv = rho > 0.0 ? -0.5 * Aemb / sr : 0.0;
-        if (PREC == MD_PREC_FP64) V.fp64[p] = fpv;
-        else V.fp32[p] = (float)fpv;
+        if (PREC == MD_PREC_FP64) {
+            V.fp64[p] = fpv;
+        } else {
+            // single element: the record's type slot is free until the next drift
+            // rewrites it, so F'(rho) rides in rec.w and the force pass gathers
+            // one 16-byte record per pair instead of two separate loads
+            V.rec[p].w = (float)fpv;
+        }
         if (a.mode == kModeEV) V.emb[p] = rho > 0.0 ? -Aemb * sr : 0.0;
     }
 }
@@ -429,9 +435,10 @@ struct EamPair {
     real rx, ry, rz;
     __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
     __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
-    __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int) {
+    __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int wj) {
         if (r2 < rc2) {
-            const real fpj = Pol<PREC>::fp(*V, entry_j(ent));
+            // mixed: F'_j came with the record (rec.w, set by the density pass)
+            const real fpj = (PREC == MD_PREC_FP64) ? Pol<PREC>::fp(*V, entry_j(ent)) : (real)__int_as_float(wj);
             const real rinv = Pol<PREC>::rsqrt(r2);
             const real r = r2 * rinv;
             const real t = rc - r;
@@ -484,7 +491,7 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
             const int cnt = V.ncount[p];
             real xi, yi, zi;
             P::load(V, p, xi, yi, zi, ti);
-            pr.fpi = P::fp(V, p);
+            pr.fpi = (PREC == MD_PREC_FP64) ? P::fp(V, p) : (real)__int_as_float(ti);
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
             walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
         }
@@ -498,8 +505,10 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
         for (int k = 0; k < 6; ++k) w_acc[k] = group_sum<T>(pr.w[k].value());
     }
     if (valid && sub == 0) {
-        epilogue(V, a.mode, rem, p, ti, fx, fy, fz, s_ftm);
-        if (EV) write_ev(V, p, ti, e_acc + V.emb[p], w_acc, s_ftm);
+        // single element (checked at creation): type 0 for the mass; in the mixed
+        // path the loaded record's .w holds F'(rho), not a type
+        epilogue(V, a.mode, rem, p, 0, fx, fy, fz, s_ftm);
+        if (EV) write_ev(V, p, 0, e_acc + V.emb[p], w_acc, s_ftm);
     }
     finish_step(V, a);
 }

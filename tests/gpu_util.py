@@ -66,3 +66,9 @@ def oracle_pairs(ref):
 
 def margin_ok(x, box, rl, idx=None, margin=1e-9):
     return oracle.min_gap(x, box, rl, idx) > margin
+
+
+# FP32 resolves distances near rc only to ~1e-7 rc: a pair closer than this to
+# the cut-off may be counted differently from FP64 (the unshifted LJ force jumps
+# there), so mixed-precision force parity inputs keep pairs this far from rc
+RC_MARGIN_MIXED = 1e-6

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import TOL_FP64, TOL_MIXED, TPAS, rel_maxnorm
+from gpu_util import RC_MARGIN_MIXED, TOL_FP64, TOL_MIXED, TPAS, rel_maxnorm
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,7 @@ def lj864k(request):
     x, box = d["x"], d["box"]
     idx = sample(x.shape[0], 40 if rc == 2.5 else 24, seed=int(rc * 10))
     assert oracle.min_gap(x, box, rc + SKIN, idx) > 1e-9
+    assert oracle.min_gap(x, box, rc, idx) > RC_MARGIN_MIXED
     f, _, _ = oracle.lj_at(x, box, rc, idx)
     nbr = oracle.neighbors(x, box, rc + SKIN, idx)
     return dict(d, idx=idx, f=f, nbr=nbr)
@@ -73,6 +74,7 @@ def test_lj864k_steps_keep_parity():
         x, _, f = (a.cpu().numpy() for a in s.state())
         assert s.info()["rebuilds"] >= 2
     idx = sample(x.shape[0], 32, seed=9)
+    assert oracle.min_gap(x, d["box"], 2.5, idx) > RC_MARGIN_MIXED
     fr, _, _ = oracle.lj_at(x, d["box"], 2.5, idx)
     assert rel_maxnorm(f[idx], fr) < TOL_MIXED
 
@@ -82,6 +84,7 @@ def test_eam500k_mixed_and_fp64():
     d = synth.config2(displacement=0.1)
     x, box = d["x"], d["box"]
     idx = sample(x.shape[0], 12, seed=3)
+    assert oracle.min_gap(x, box, d["rc"], idx) > RC_MARGIN_MIXED
     fr, rho = oracle.eam_at(x, box, d["eam"], idx)
     for prec, tol in (("mixed", TOL_MIXED), ("fp64", TOL_FP64)):
         with System.eam(x, d["v"], box, eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
