@@ -239,7 +239,7 @@ def run_reference(args, ws, rank):
     oracle.lj_at(d["x"], d["box"], 2.5, probe)
     per_atom = (time.perf_counter() - t0) / 4
     total = max(1, args.steps + args.warmup)
-    m = int(max(1, min(5000, 100.0 / total / max(per_atom, 1e-9))))
+    m = int(max(1, min(5000, n, 100.0 / total / max(per_atom, 1e-9))))
     for _ in range(args.warmup):
         oracle.lj_at(d["x"], d["box"], 2.5, rng.choice(n, m, replace=False))
     t0 = time.perf_counter()
