@@ -227,6 +227,18 @@ typedef struct {
  */
 md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_out, double *bytes_out);
 
+/*
+ * Time the memory-only twin of the force pass (mixed-precision LJ, full
+ * list): the same list stream, record gathers and velocity read/write as
+ * md_step's force kernel in the current variant, with three additions per
+ * pair instead of the pair arithmetic -- the ceiling of the force pass's
+ * access pattern on this GPU.  ms_out (host): average milliseconds per pass
+ * over `reps` launches after `warmup`; state unchanged.  MD_ERR_UNSUPPORTED
+ * for other potentials, precisions or list kinds.  For measurement only; the
+ * paper has no counterpart.  Synchronises.
+ */
+md_status md_time_gather(md_system *h, int32_t warmup, int32_t reps, double *ms_out);
+
 /* Statistics (synchronises). */
 md_status md_info(md_system *h, md_info_t *out);
 

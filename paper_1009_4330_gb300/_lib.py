@@ -19,7 +19,7 @@ MD_MAX_TYPES = 8
 EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "md_compute_forces", "md_step",
            "md_energy_virial", "md_get_state", "md_set_state", "md_set_params", "md_forces_backward",
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
-           "md_time_force", "md_step_eager", "md_neighbors_noalloc")
+           "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather")
 
 
 class MdConfig(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(build_if_missing: bool = True):
         "md_get_neighbors": [vp, vp, vp, i32],
         "md_sync_status": [vp],
         "md_time_force": [vp, i32, i32, P(d), P(d)],
+        "md_time_gather": [vp, i32, i32, P(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

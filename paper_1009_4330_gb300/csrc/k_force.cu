@@ -322,6 +322,69 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
     if (!HALF) finish_step(V, a);
 }
 
+// Memory-only twin of the mixed full-list force pass, for measuring the
+// ceiling of its access pattern: the same list walk and record gathers, the
+// same velocity read/write (with a zero increment), but three additions per
+// pair instead of the pair arithmetic and compensated sums.
+struct GatherPair {
+    float acc;
+    __device__ __forceinline__ void round_begin() {}
+    __device__ __forceinline__ void round_end() {}
+    __device__ __forceinline__ void operator()(uint32_t, float dx, float dy, float dz, float, int) { acc += dx + dy + dz; }
+};
+
+template <int T, int Q>
+__global__ void __launch_bounds__(256, 4) k_gather_probe(View V, KArgs a) {
+    using P = Pol<MD_PREC_MIXED>;
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    GatherPair pr;
+    pr.acc = 0.f;
+    bool valid = false;
+    if (gw * A < V.n_pad) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            const int cnt = V.ncount[p];
+            float xi, yi, zi;
+            int ti;
+            P::load(V, p, xi, yi, zi, ti);
+            const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
+            walk_list<MD_PREC_MIXED, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
+        }
+    }
+    const double sum = group_sum<T>((double)pr.acc);
+    if (valid && sub == 0) {
+        const int n = V.n_pad;
+        const double z = sum * 0.0;  // not foldable: sum may be NaN/Inf only if the state is
+        V.v[p] += z;
+        V.v[n + p] += z;
+        V.v[2 * n + p] += z;
+    }
+}
+
+template <int Q>
+static const void *pick_probe_q(int T) {
+    switch (T) {
+        case 1: return (const void *)k_gather_probe<1, Q>;
+        case 2: return (const void *)k_gather_probe<2, Q>;
+        case 4: return (const void *)k_gather_probe<4, Q>;
+        case 8: return (const void *)k_gather_probe<8, Q>;
+        case 16: return (const void *)k_gather_probe<16, Q>;
+        default: return (const void *)k_gather_probe<32, Q>;
+    }
+}
+
+void gather_probe_sequence(const View &V, int block, std::vector<KCall> &seq) {
+    KArgs a{};
+    const long long threads = (long long)V.n_pad * V.tpa;
+    const void *fn = V.vec == 4 ? pick_probe_q<4>(V.tpa) : (V.vec == 2 ? pick_probe_q<2>(V.tpa) : pick_probe_q<1>(V.tpa));
+    seq.push_back(KCall{fn, dim3((unsigned)((threads + block - 1) / block)), dim3(block), 0, a});
+}
+
 // zero F before a half-list pass
 __global__ void k_zero_f(View V, KArgs a) {
     const int n3 = 3 * V.n_pad;

@@ -887,6 +887,28 @@ md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_o
     return MD_OK;
 }
 
+md_status md_time_gather(md_system *h, int32_t warmup, int32_t reps, double *ms_out) {
+    if (!h || !ms_out || reps < 1 || warmup < 0) return fail(h, MD_ERR_INVALID, "bad argument");
+    if (h->cfg.pot != MD_POT_LJ || h->V.prec != MD_PREC_MIXED || h->V.half)
+        return fail(h, MD_ERR_UNSUPPORTED, "md_time_gather: mixed-precision LJ with a full list only");
+    std::vector<KCall> seq;
+    gather_probe_sequence(h->V, h->block, seq);
+    for (int w = 0; w < warmup; ++w) CK(h, run_seq(h, seq));
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    CK(h, cudaEventRecord(e0, h->s));
+    for (int r = 0; r < reps; ++r) CK(h, run_seq(h, seq));
+    CK(h, cudaEventRecord(e1, h->s));
+    CK(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = (double)ms / reps;
+    return MD_OK;
+}
+
 md_status md_info(md_system *h, md_info_t *out) {
     if (!h || !out) return fail(h, MD_ERR_INVALID, "null argument");
     Ctl c;

@@ -30,6 +30,9 @@ void drift_sequence(const View &V, bool in_graph, std::vector<KCall> &seq);
 // kModeEV).  `block` = threads per block.
 void force_sequence(const View &V, int mode, int block, bool in_graph, std::vector<KCall> &seq);
 
+// memory-only twin of the mixed full-list LJ force pass (see md_time_gather)
+void gather_probe_sequence(const View &V, int block, std::vector<KCall> &seq);
+
 // loop-control kernel placed before the md_step WHILE node
 void loop_init_sequence(const View &V, std::vector<KCall> &seq);
 

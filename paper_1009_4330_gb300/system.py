@@ -248,6 +248,12 @@ class System:
     def sync_status(self):
         self._call("md_sync_status")
 
+    def time_gather(self, warmup=3, reps=20):
+        """ms per pass of the force kernel's memory-only twin (mixed LJ, full list)"""
+        ms = ctypes.c_double()
+        self._call("md_time_gather", ctypes.c_int32(warmup), ctypes.c_int32(reps), ctypes.byref(ms))
+        return ms.value
+
     def time_force(self, warmup=3, reps=20):
         """(ms per force pass as md_step runs it, algorithmic DRAM bytes per pass)"""
         ms = ctypes.c_double()
