@@ -275,6 +275,13 @@ __device__ __noinline__ bool in_list_fp64(const View &V, const Rep &R, int p, in
     return d0 * d0 + d1 * d1 + d2 * d2 < V.rl2;
 }
 
+// three-input minimum (one instruction on sm_100 and later)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // 32 x 32 bit-matrix transpose across a warp: on entry lane r holds row r
 // (bit c = M[r][c]); on return lane c holds column c (bit r = M[r][c]).
 // Five butterfly stages of recursive 2x2 block swaps.
@@ -293,22 +300,36 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 // Verlet list of every atom of a rebuilding replica: all j in the 27 cells
 // around i's cell with |x_i - x_j| < rl.  One warp per home cell (home atoms
 // in chunks of 32).  The 27 neighbour cells form 9 rows of 3 x-adjacent
-// cells; lanes 0..26 fetch the 27 cell bounds at once.  Each row is walked as
-// one flat candidate range, 32 candidates at a time, one per lane, held in
-// registers already shifted into the home cell's frame.  Each lane tests its
-// candidate against every home atom (records broadcast from shared memory)
-// into a 32-bit acceptance mask; a warp bit-matrix transpose turns the
+// cells; lanes 0..26 fetch the 27 cell bounds at once.  Each row is read as
+// one flat candidate range, 32 candidates at a time, one per lane, shifted
+// into the home cell's frame.  A candidate farther than rl from the bounding
+// box of the home atoms cannot be accepted by any of them (about a quarter of
+// the 27-cell volume); the others go to a per-warp queue in shared memory, in
+// candidate order, and are tested in full rounds of 32.  In a round each lane
+// tests its candidate against every home atom (records broadcast from shared
+// memory) into a 32-bit acceptance mask; a warp bit-matrix transpose turns the
 // candidates' masks into each home atom's mask of accepted candidates, and
 // each home-atom lane appends them to its list in candidate order (warp
 // ballot/prefix compaction in transposed form: deterministic lists, no
 // divergent per-pair bookkeeping).  The test is FP32 with a margin far above
 // its rounding error; pairs inside the margin band are decided in FP64, so
 // the list equals the FP64 definition exactly.  HALF keeps j > i only.
+constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
+constexpr int kBatch = 14;  // rounds whose list entries are appended together
+
 template <int PREC, int HALF>
 __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
     __shared__ float4 s_h[8][32];
+    __shared__ float4 s_q[8][kQueue];  // shifted candidate position, .w = list entry bits
+    __shared__ float4 s_box[8][2];     // bounding box of the home chunk: lo, hi
+    __shared__ int2 s_cell[8][27];     // neighbour cells: first slot, count
+    __shared__ uint32_t s_st[8][4][32];  // per home atom: its open group of 4 entries
+    __shared__ uint32_t s_t[8][kBatch][32];  // per round: home atom's mask of accepted candidates
+    __shared__ uint32_t s_e[8][kBatch][32];  // per round: candidate's list entry
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gb = blockIdx.x * 8 + w;
+    // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
+    const int gw = blockIdx.x * 8 + w;
+    const int gb = gw / V.hsplit, part = gw - gb * V.hsplit;
     int my_max = 0;
     long long my_sum = 0;
     int my_rep = -1;
@@ -324,7 +345,6 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
             const int bx = unpack_bx(xyz), by = unpack_by(xyz), bz = unpack_bz(xyz);
             const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
             // neighbour cell (row = lane / 3, dx = lane % 3 - 1) bounds, one lane each
-            int my_st = 0, my_ct = 0;
             if (lane < 27) {
                 const int row = lane / 3;
                 const int dx = lane - 3 * row - 1, dy = row % 3 - 1, dz = row / 3 - 1;
@@ -333,12 +353,13 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                 cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
                 cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
                 const int nbin = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
-                my_st = V.bin_start[nbin];
-                my_ct = V.bin_count[nbin];
+                s_cell[w][lane] = make_int2(V.bin_start[nbin], V.bin_count[nbin]);
             }
             const int hs = V.bin_start[gb], hn = V.bin_count[gb];
             const float rl2f = 0.5f * (V.rl2f_lo + V.rl2f_hi), margin = 0.5f * (V.rl2f_hi - V.rl2f_lo);
-            for (int h0 = 0; h0 < hn; h0 += 32) {
+            // box pre-test bound: above every squared distance the margin band can hold
+            const float keep2 = V.rl2f_hi + margin;
+            for (int h0 = 32 * part; h0 < hn; h0 += 32 * V.hsplit) {
                 const int nh = min(32, hn - h0);
                 const int hbase = hs + h0;  // slot of home atom 0 of this chunk
                 __syncwarp();
@@ -348,6 +369,25 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                     if (lane < nh) hr = V.rec[hbase + lane];
                     hr.w = hr.x * hr.x + hr.y * hr.y + hr.z * hr.z;
                     s_h[w][lane] = hr;
+                    // bounding box of the chunk's home atoms
+                    const bool in = lane < nh;
+                    float lox = in ? hr.x : 3.0e38f, hix = in ? hr.x : -3.0e38f;
+                    float loy, loz, hiy, hiz;
+                    loy = in ? hr.y : 3.0e38f; hiy = in ? hr.y : -3.0e38f;
+                    loz = in ? hr.z : 3.0e38f; hiz = in ? hr.z : -3.0e38f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+                        loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+                        loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
+                        hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+                        hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+                        hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
+                    }
+                    if (lane == 0) {
+                        s_box[w][0] = make_float4(lox, loy, loz, 0.f);
+                        s_box[w][1] = make_float4(hix, hiy, hiz, 0.f);
+                    }
                 }
                 __syncwarp();
                 // this lane as a home atom: its list
@@ -355,82 +395,150 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
                 size_t slot = (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
                 const int jump = (32 << lq) - (tq - 1);
                 int mycnt = 0;
-#pragma unroll 1
-                for (int row = 0; row < 9; ++row) {
-                    const int n0 = __shfl_sync(0xffffffffu, my_ct, 3 * row);
-                    const int n1 = __shfl_sync(0xffffffffu, my_ct, 3 * row + 1);
-                    const int n2 = __shfl_sync(0xffffffffu, my_ct, 3 * row + 2);
-                    const int s0 = __shfl_sync(0xffffffffu, my_st, 3 * row);
-                    const int s1 = __shfl_sync(0xffffffffu, my_st, 3 * row + 1);
-                    const int s2 = __shfl_sync(0xffffffffu, my_st, 3 * row + 2);
-                    const int m = n0 + n1 + n2;
-                    const int dy = row % 3 - 1, dz = row / 3 - 1;
-                    const bool self_row = (dy == 0 && dz == 0);
-                    const float oy = dy * hy, oz = dz * hz;
-                    const uint32_t rcode = ((uint32_t)(dz + 1) << 4) | ((uint32_t)(dy + 1) << 2);
-#pragma unroll 1
-                    for (int c0 = 0; c0 < m; c0 += 32) {
-                        // this lane as a candidate, shifted into the home frame
-                        const int f = c0 + lane;
-                        int j = 0, seg = 0;
-                        float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
-                        if (f < m) {
-                            seg = (f >= n0) + (f >= n0 + n1);
-                            j = seg == 0 ? s0 + f : (seg == 1 ? s1 + f - n0 : s2 + f - n0 - n1);
-                            const float4 rj = V.rec[j];
-                            qx = rj.x + (seg - 1) * hx;
-                            qy = rj.y + oy;
-                            qz = rj.z + oz;
+                int qn = 0;  // queued candidates (warp-uniform)
+                // append the batch's accepted candidates to the home atoms' lists,
+                // round by round in candidate order: each home-atom lane walks its
+                // own masks, so the loop runs as long as the longest share of the
+                // batch rather than the sum of each round's longest share
+                int rb = 0;  // rounds in the pending batch (warp-uniform)
+                auto append = [&]() {
+                    __syncwarp();
+                    int r = 0;
+                    unsigned t = s_t[w][0][lane];
+                    while (t == 0u && ++r < rb) t = s_t[w][r][lane];
+                    while (__any_sync(0xffffffffu, r < rb)) {
+                        if (r < rb) {
+                            const uint32_t ec = s_e[w][r][__ffs(t) - 1];
+                            if (tq >= 4) {
+                                s_st[w][mycnt & 3][lane] = ec;
+                                if ((mycnt & 3) == 3 && mycnt < maxn)
+                                    *(uint4 *)(V.nlist + slot - 3) =
+                                        make_uint4(s_st[w][0][lane], s_st[w][1][lane], s_st[w][2][lane], ec);
+                            } else if (mycnt < maxn) {
+                                V.nlist[slot] = ec;
+                            }
+                            ++mycnt;
+                            slot += (mycnt & (tq - 1)) ? 1 : jump;
+                            t &= t - 1u;
+                            while (t == 0u && ++r < rb) t = s_t[w][r][lane];
                         }
-                        const uint32_t e = ((uint32_t)j << 6) | (uint32_t)seg | rcode;
-                        // acceptance bits over the home atoms, 8 at a time with
-                        // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
-                        // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
-                        // < ~1e-5 rl^2 here, far inside the margin); the sign bit of t
-                        // is the decision, and the smallest |t| flags the margin band.
-                        const float qx2 = -2.0f * qx, qy2 = -2.0f * qy, qz2 = -2.0f * qz;
-                        const float q2m = qx * qx + qy * qy + qz * qz - rl2f;
-                        unsigned acc = 0u;
-                        float tmin = 3.0e38f;
+                    }
+                    __syncwarp();
+                    rb = 0;
+                };
+                // one round: queue entries 0..cnt-1 (cnt <= 32), one per lane
+                auto round = [&](int cnt) {
+                    float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
+                    uint32_t e = 0u;
+                    if (lane < cnt) {
+                        const float4 c = s_q[w][lane];
+                        qx = c.x; qy = c.y; qz = c.z;
+                        e = __float_as_uint(c.w);
+                    }
+                    // acceptance bits over the home atoms, 8 at a time with
+                    // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
+                    // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
+                    // < ~1e-5 rl^2 here, far inside the margin); the sign bit of t
+                    // is the decision, and the smallest |t| flags the margin band.
+                    const float qx2 = -2.0f * qx, qy2 = -2.0f * qy, qz2 = -2.0f * qz;
+                    const float q2m = qx * qx + qy * qy + qz * qz - rl2f;
+                    unsigned acc = 0u;
+                    float tmin = 3.0e38f;
+                    // home atoms from the top down, 8 at a time: each test shifts its
+                    // sign bit in at bit 0, so that home atom h ends at bit h
 #pragma unroll 1
-                        for (int hb = 0; hb < nh; hb += 8) {
-                            unsigned a8 = 0u;
+                    for (int hb = (nh - 1) & ~7; hb >= 0; hb -= 8) {
+                        float t8[8];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const float4 ri = s_h[w][hb + k];
-                                const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
-                                a8 |= (__float_as_uint(t) >> 31) << k;
-                                tmin = fminf(tmin, fabsf(t));
-                            }
-                            acc |= a8 << hb;
+                        for (int k = 7; k >= 0; --k) {
+                            const float4 ri = s_h[w][hb + k];
+                            t8[k] = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                            acc = __funnelshift_l(__float_as_uint(t8[k]), acc, 1);
                         }
-                        if (tmin < margin) {  // margin band: decide those pairs in FP64 (rare)
-                            for (int h = 0; h < nh; ++h) {
-                                const float4 ri = s_h[w][h];
-                                const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
-                                if (fabsf(t) < margin) {
-                                    const bool in = in_list_fp64<PREC>(V, R, hbase + h, j, seg - 1, dy, dz);
-                                    acc = in ? (acc | (1u << h)) : (acc & ~(1u << h));
-                                }
-                            }
-                        }
-                        // exclusions: the atom itself; for HALF every home atom with slot >= j
-                        const int jh = j - hbase;  // j as a home-atom index, if it is one
-                        if (self_row && seg == 1 && jh >= 0 && jh < 32) acc &= ~(1u << jh);
-                        if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
-                        // lane = home atom: bit c set if candidate lane c is accepted
-                        unsigned t = warp_transpose32(acc, lane);
-                        while (__any_sync(0xffffffffu, t != 0u)) {
-                            const int c = t ? __ffs(t) - 1 : lane;
-                            const uint32_t ec = __shfl_sync(0xffffffffu, e, c);
-                            if (t) {
-                                t &= t - 1u;
-                                if (mycnt < maxn) V.nlist[slot] = ec;
-                                ++mycnt;
-                                slot += (mycnt & (tq - 1)) ? 1 : jump;
+#pragma unroll
+                        for (int k = 0; k < 8; k += 2) tmin = fmin3(tmin, fabsf(t8[k]), fabsf(t8[k + 1]));
+                    }
+                    const int j = (int)(e >> 6);
+                    if (tmin < margin) {  // margin band: decide those pairs in FP64 (rare)
+                        for (int h = 0; h < nh; ++h) {
+                            const float4 ri = s_h[w][h];
+                            const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                            if (fabsf(t) < margin) {
+                                const bool in = in_list_fp64<PREC>(V, R, hbase + h, j, entry_dx(e), entry_dy(e),
+                                                                    entry_dz(e));
+                                acc = in ? (acc | (1u << h)) : (acc & ~(1u << h));
                             }
                         }
                     }
+                    // exclusions: the atom itself; for HALF every home atom with slot >= j
+                    const int jh = j - hbase;  // j as a home-atom index, if it is one
+                    if ((e & 63u) == 21u && jh >= 0 && jh < 32) acc &= ~(1u << jh);
+                    if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
+                    // lane = home atom: bit c set if candidate lane c is accepted;
+                    // kept with the round's entries until the batch is appended
+                    s_t[w][rb][lane] = warp_transpose32(acc, lane);
+                    s_e[w][rb][lane] = e;
+                    if (++rb == kBatch) append();
+                };
+                // fill the queue from the rows in order until it holds a full
+                // round (or the rows are done), then run the round
+                int row = 0, c0 = 0;
+                int m = s_cell[w][0].y + s_cell[w][1].y + s_cell[w][2].y;
+#pragma unroll 1
+                while (true) {
+#pragma unroll 1
+                    while (qn < 32 && row < 9) {
+                        // this lane as a candidate, shifted into the home frame,
+                        // kept if within rl (plus the band) of the home bounding box
+                        const int f = c0 + lane;
+                        bool keep = false;
+                        float4 c;
+                        if (f < m) {
+                            const int dy = row % 3 - 1, dz = row / 3 - 1;
+                            const int2 c0_ = s_cell[w][3 * row], c1_ = s_cell[w][3 * row + 1];
+                            const int seg = (f >= c0_.y) + (f >= c0_.y + c1_.y);
+                            const int j = seg == 0 ? c0_.x + f
+                                                   : (seg == 1 ? c1_.x + f - c0_.y
+                                                               : s_cell[w][3 * row + 2].x + f - c0_.y - c1_.y);
+                            const float4 rj = V.rec[j];
+                            c.x = rj.x + (seg - 1) * hx;
+                            c.y = rj.y + dy * hy;
+                            c.z = rj.z + dz * hz;
+                            c.w = __uint_as_float(((uint32_t)j << 6) | (uint32_t)seg | ((uint32_t)(dz + 1) << 4) |
+                                                  ((uint32_t)(dy + 1) << 2));
+                            const float4 lo = s_box[w][0], hi = s_box[w][1];
+                            const float bx_ = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
+                            const float by_ = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
+                            const float bz_ = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
+                            keep = bx_ * bx_ + by_ * by_ + bz_ * bz_ < keep2;
+                        }
+                        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                        if (keep) s_q[w][qn + __popc(kb & ((1u << lane) - 1u))] = c;
+                        qn += __popc(kb);
+                        c0 += 32;
+                        if (c0 >= m) {
+                            c0 = 0;
+                            ++row;
+                            if (row < 9)
+                                m = s_cell[w][3 * row].y + s_cell[w][3 * row + 1].y + s_cell[w][3 * row + 2].y;
+                        }
+                    }
+                    if (qn == 0) break;
+                    const int cnt = min(qn, 32);
+                    __syncwarp();
+                    round(cnt);
+                    qn -= cnt;
+                    __syncwarp();
+                    float4 rest;
+                    if (lane < qn) rest = s_q[w][32 + lane];
+                    __syncwarp();
+                    if (lane < qn) s_q[w][lane] = rest;
+                    __syncwarp();
+                }
+                if (rb > 0) append();
+                if (tq >= 4 && lane < nh && (mycnt & 3) && mycnt <= maxn) {
+                    const size_t g = slot - (mycnt & 3);
+                    for (int q = 0; q < (mycnt & 3); ++q) V.nlist[g + q] = s_st[w][q][lane];
                 }
                 if (lane < nh) {
                     V.ncount[p] = min(mycnt, maxn);
@@ -506,7 +614,7 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
         kb = V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>;
     else
         kb = V.half ? (const void *)k_build<MD_PREC_MIXED, 1> : (const void *)k_build<MD_PREC_MIXED, 0>;
-    seq.push_back(KCall{kb, dim3((V.nbins_total + 7) / 8), dim3(256), 0, a});
+    seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + 7) / 8), dim3(256), 0, a});
 }
 
 }  // namespace md

@@ -421,6 +421,12 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.n_tiles = tile0;
     V.n_rep = n_rep;
     V.nbins_total = bin0;
+    {
+        // enough warps per cell that a cell's home chunks of 32 atoms run side by side
+        double mean = 0.0;
+        for (const Rep &R : h->reps) mean = std::max(mean, (double)R.natoms / (double)R.nbins);
+        V.hsplit = std::max(1, std::min(8, (int)std::ceil(1.15 * mean / 32.0)));
+    }
     V.prec = h->cfg.prec;
     V.pot = h->cfg.pot;
     V.ntypes = h->cfg.n_types;

@@ -86,6 +86,7 @@ struct PairTab {
 // CUDA graphs; any reallocation rebuilds the graphs).
 struct View {
     int n_pad, n_tiles, n_rep, nbins_total, maxneigh;
+    int hsplit;  // warps per cell in the list build (home chunks of 32 shared out)
     int tpa;          // threads per atom the list is laid out for
     int vec;          // entries per thread per list load (1, 2 or 4)
     int ltpa, lvec;   // log2 of tpa and vec
