@@ -72,6 +72,8 @@ def _load():
     lib.oracle_eam.restype = ctypes.c_int
     lib.oracle_eam.argtypes = [_I64, _d, _d, _d, _d, _d, _d, _d, _d]
     lib.oracle_eam_at.restype = ctypes.c_int
+    lib.oracle_eam_vjp.restype = ctypes.c_int
+    lib.oracle_eam_vjp.argtypes = [_I64, _d, _d, _d, _d, _d, _d]
     lib.oracle_eam_at.argtypes = [_I64, _d, _d, _d, _I64, _i64, _d, _d]
     lib.oracle_kinetic.restype = _D
     lib.oracle_kinetic.argtypes = [_I64, _d, _i32, _d, _D]
@@ -245,6 +247,19 @@ def eam_at(x, box, p, idx):
     _check(lib.oracle_eam_at(x.shape[0], _pd(x), _pd(_f64(box)), _pd(_f64(p)), m, _pi64(idx), _pd(f), _pd(rho)),
            "eam_at")
     return f, rho
+
+
+def eam_vjp(x, box, p, g):
+    """Backward of the EAM forces for L = sum_i g_i.F_i: (grad_x (n,3), grad_p (5,)) with grad_p in the
+    layout of p = (rc, A, c0, c1, c2); the cut-off slot is 0 (not differentiated)."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    g = _f64(g, (n, 3))
+    gx = np.zeros((n, 3))
+    gp = np.zeros(5)
+    _check(lib.oracle_eam_vjp(n, _pd(x), _pd(_f64(box)), _pd(_f64(p)), _pd(g), _pd(gx), _pd(gp)), "eam_vjp")
+    return gx, gp
 
 
 def kinetic(v, mass, types=None, ftm2v=1.0) -> float:

@@ -430,6 +430,110 @@ int oracle_eam_at(int64_t n, const double *x, const double box[3], const double 
     return 0;
 }
 
+/*
+ * Backward of the EAM forces for the loss L = sum_i g_i . F_i (the
+ * vector-Jacobian product that force matching needs; the forward is
+ * oracle_eam).  Derivation, with d = x_i - x_j, r = |d|, u = d / r,
+ * G = g_i - g_j, w = G . u, and per pair
+ *     s = phi'(r) + (F'_i + F'_j) rho'(r)      so that F_i = -sum_j s u,
+ *     k = phi''(r) + (F'_i + F'_j) rho''(r)    (ds/dr with F' held fixed):
+ *   1. L depends on F'_m explicitly through s: dL/dF'_m = -lambda_m with
+ *      lambda_m = sum_j w_mj rho'(r_mj);
+ *   2. F'_m depends on rho_m: dL/drho_m = -mu_m, mu_m = lambda_m F''(rho_m);
+ *   3. positions, through s and u at fixed F', and through every rho:
+ *      dL/dx_i = -sum_j [ (s/r) G + w (k - s/r) u + (mu_i + mu_j) rho'(r) u ];
+ *   4. parameters: dL/dA = -sum_m lambda_m dF'_m/dA with dF'/dA = -1/(2 sqrt(rho)),
+ *      dL/dc_q = -sum_i sum_j (g_i . u) d phi'(r)/dc_q.
+ * grad_p has the layout of p; its cut-off slot grad_p[0] is not a
+ * derivative (the cut-off is not differentiated) and is written as 0.
+ * g, grad_x: n*3.  grad_x or grad_p may be NULL.
+ */
+static double fs_d2phi(double r, const double *p) {
+    double t = p[0] - r;
+    return 2.0 * (p[2] + p[3] * r + p[4] * r * r) - 4.0 * t * (p[3] + 2.0 * p[4] * r) + t * t * 2.0 * p[4];
+}
+static double fs_d2rho(void) { return 2.0; }
+static double fs_d2embed(double rho, double A) { return rho > 0.0 ? 0.25 * A / (rho * sqrt(rho)) : 0.0; }
+static double fs_dembed_dA(double rho) { return rho > 0.0 ? -0.5 / sqrt(rho) : 0.0; }
+/* d phi'(r) / d c_q for q = 0, 1, 2 */
+static void fs_dphi_dc(double r, double rc, double out[3]) {
+    double t = rc - r;
+    out[0] = -2.0 * t;
+    out[1] = -2.0 * t * r + t * t;
+    out[2] = -2.0 * t * r * r + 2.0 * r * t * t;
+}
+
+int oracle_eam_vjp(int64_t n, const double *x, const double box[3], const double *p, const double *g,
+                   double *grad_x, double *grad_p) {
+    const double rc = p[0], A = p[1];
+    if (n <= 0 || rc <= 0.0 || !box_ok(box, rc)) return -1;
+    const double rc2 = rc * rc;
+    double *rho = (double *)malloc(sizeof(double) * (size_t)n);
+    double *fp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *lam = (double *)malloc(sizeof(double) * (size_t)n);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)n);
+    double *gc_i = (double *)calloc((size_t)n * 3, sizeof(double));
+    if (!rho || !fp || !lam || !mu || !gc_i) { free(rho); free(fp); free(lam); free(mu); free(gc_i); return -1; }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        rho[i] = fs_density(n, x, i, box, rc);
+        fp[i] = fs_dembed(rho[i], A);
+    }
+    /* step 1: lambda_i = sum_j ((g_i - g_j) . u_ij) rho'(r_ij) */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double l = 0.0, d[3];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r2 = separation(x, i, j, box, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), w = 0.0;
+            for (int a = 0; a < 3; ++a) w += (g[3 * i + a] - g[3 * j + a]) * d[a] / r;
+            l += w * fs_drho(r, rc);
+        }
+        lam[i] = l;
+    }
+    /* step 2 */
+    for (int64_t i = 0; i < n; ++i) mu[i] = lam[i] * fs_d2embed(rho[i], A);
+    /* steps 3 and 4 (c part) */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0}, d[3];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r2 = separation(x, i, j, box, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), u[3], G[3], w = 0.0, gu = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                u[a] = d[a] / r;
+                G[a] = g[3 * i + a] - g[3 * j + a];
+                w += G[a] * u[a];
+                gu += g[3 * i + a] * u[a];
+            }
+            double s = fs_dphi(r, p) + (fp[i] + fp[j]) * fs_drho(r, rc);
+            double k = fs_d2phi(r, p) + (fp[i] + fp[j]) * fs_d2rho();
+            double emb = (mu[i] + mu[j]) * fs_drho(r, rc);
+            for (int a = 0; a < 3; ++a) acc[a] -= (s / r) * G[a] + w * (k - s / r) * u[a] + emb * u[a];
+            double dc[3];
+            fs_dphi_dc(r, rc, dc);
+            for (int q = 0; q < 3; ++q) gc_i[3 * i + q] -= gu * dc[q];
+        }
+        if (grad_x) for (int a = 0; a < 3; ++a) grad_x[3 * i + a] = acc[a];
+    }
+    if (grad_p) {
+        double gA = 0.0, gc[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            gA -= lam[i] * fs_dembed_dA(rho[i]);
+            for (int q = 0; q < 3; ++q) gc[q] += gc_i[3 * i + q];
+        }
+        grad_p[0] = 0.0;
+        grad_p[1] = gA;
+        for (int q = 0; q < 3; ++q) grad_p[2 + q] = gc[q];
+    }
+    free(rho); free(fp); free(lam); free(mu); free(gc_i);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Kinetic energy and velocity-Verlet NVE (Sec. II)                    */
 /* ------------------------------------------------------------------ */
