@@ -382,6 +382,7 @@ def side_runs(synth, cells, K, W):
     s.close()
     # force matching: forward forces + backward (positions and 6 parameters), 32,768 atoms
     out["force_matching_32768"] = force_matching_timing(synth)
+    out["eam500000_fwd_bwd"] = eam_backward_timing(synth)
     # batched replicas (512, log-uniform 500..20000), mixed
     b = synth.config4()
     s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
@@ -426,6 +427,36 @@ def force_matching_timing(synth, reps=20):
         info = s.info()
         out[prec] = {"ms_per_fwd_bwd": ms, "pair_evaluations_per_s": 2 * info["list_entries"] / (ms / 1000),
                      "tpa": info["tpa"]}
+        s.close()
+    return out
+
+
+def eam_backward_timing(synth, reps=10):
+    """Time per forward (density + forces) + backward (dL/dx, dL/d(A, c0, c1, c2)) of
+    the 500,000-atom EAM metal, CUDA events; the backward is two FP64 list passes."""
+    import torch
+    from paper_1009_4330_gb300 import System
+    d = synth.config2(displacement=0.1)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = System.eam(d["x"], d["v"], d["box"], eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
+                       ftm2v=d["ftm2v"], precision=prec, tpa=0)
+        g = torch.ones((d["x"].shape[0], 3), dtype=torch.float64, device="cuda")
+        f = torch.empty_like(g)
+        for _ in range(3):
+            s.compute_forces(out=f)
+            s.backward(g)
+        torch.cuda.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record()
+        for _ in range(reps):
+            s.compute_forces(out=f)
+            s.backward(g)
+        e1_.record()
+        torch.cuda.synchronize()
+        ms = e0_.elapsed_time(e1_) / reps
+        info = s.info()
+        out[prec] = {"ms_per_fwd_bwd": ms, "atoms_per_s": d["x"].shape[0] / (ms / 1000), "tpa": info["tpa"]}
         s.close()
     return out
 

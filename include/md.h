@@ -161,15 +161,21 @@ md_status md_set_state(md_system *h, const double *x, const double *v);
 md_status md_set_params(md_system *h, const double *params);
 
 /*
- * Backward pass of the LJ forces for a force-matching loss: given grad_f =
+ * Backward pass of the forces for a force-matching loss (the forces of the
+ * pair-force step, App. A potentials, made differentiable): given grad_f =
  * dL/dF ([n][3], original order), write grad_x = dL/dx ([n][3], original
- * order) and grad_params = dL/dparams (device, 2*nt*nt doubles in the
- * layout of md_config.params; eps_ab is one parameter shared by the (a,b)
- * and (b,a) entries and both entries receive its derivative).  The
- * derivative is taken at fixed list: pairs at exactly r = rc contribute
+ * order) and grad_params = dL/dparams (device, in the layout of
+ * md_config.params).
+ *   LJ: 2*nt*nt doubles; eps_ab is one parameter shared by the (a,b) and
+ *       (b,a) entries and both entries receive its derivative.
+ *   EAM_FS: 5 doubles {0, dL/dA, dL/dc0, dL/dc1, dL/dc2}; the cut-off is not
+ *       differentiated and its slot is written as 0.  The chain rule runs
+ *       through F'(rho): one list pass for rho_i and the loss's sensitivity to
+ *       F'_i, a second for the position and c gradients.
+ * The derivative is taken at fixed list: pairs at exactly r = rc contribute
  * nothing.  Pair terms and sums are in double precision in both modes.
- * grad_x or grad_params may be NULL.  Uses the current neighbour list.
- * LJ only (MD_ERR_UNSUPPORTED otherwise).
+ * grad_x or grad_params may be NULL.  Uses the current neighbour list, which
+ * must be a full list (MD_ERR_UNSUPPORTED for a half list).
  */
 md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x, double *grad_params);
 

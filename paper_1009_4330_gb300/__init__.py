@@ -8,6 +8,6 @@ simulations on GPU-based clusters" (LAMMPS_CUDA).
 """
 from ._build import build as build_library  # noqa: F401
 from ._lib import load as load_library  # noqa: F401
-from .system import LJForces, MDError, System, lj_params, pairs_to_matrix  # noqa: F401
+from .system import EAMForces, LJForces, MDError, System, lj_params, pairs_to_matrix  # noqa: F401
 
-__all__ = ["System", "LJForces", "MDError", "lj_params", "pairs_to_matrix", "build_library", "load_library"]
+__all__ = ["System", "LJForces", "EAMForces", "MDError", "lj_params", "pairs_to_matrix", "build_library", "load_library"]

@@ -251,6 +251,177 @@ __global__ void k_gp_reduce(View V, int nblocks, double *grad_params) {
     g[tb * nt + ta] = s;
 }
 
+// ---------------------------------------------------------- EAM backward ----
+// Vector-Jacobian product of the Finnis-Sinclair forces (App. A EAM form)
+// for L = sum_i g_i.F_i, in two passes over the full list.  With d = x_i - x_j,
+// r = |d|, u = d/r, G = g_i - g_j, w = G.u, s = phi' + (F'_i + F'_j) rho' and
+// k = phi'' + (F'_i + F'_j) rho'':
+//   pass 1: rho_i and lambda_i = sum_j w rho'(r); then F'_i, mu_i = lambda_i F''(rho_i)
+//           and the atom's share -lambda_i dF'_i/dA of dL/dA;
+//   pass 2: dL/dx_i = -sum_j [(s/r) G + (w (k - s/r) + (mu_i + mu_j) rho') u]
+//           and dL/dc_q = -sum_j (g_i.u) dphi'/dc_q.
+// All in FP64 in both precision modes.
+
+// this thread's share of atom p's list, in the list layout: entries r T Q + sub Q + q
+template <typename F>
+__device__ __forceinline__ void for_list(const View &V, int p, int sub, int T, F &&f) {
+    const int cnt = V.ncount[p], Q = V.vec, maxn = V.maxneigh;
+    for (int k0 = sub * Q; k0 < cnt; k0 += T * Q)
+        for (int k = k0; k < k0 + Q && k < cnt; ++k) f(V.nlist[list_index(p, k, V.ltpa, V.lvec, maxn)]);
+}
+
+template <int T>
+__device__ __forceinline__ double tgroup_sum(double x) {
+    for (int o = T / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// block sum of one value per thread, in warp order, into gp_part[blk * 4 + slot]
+__device__ __forceinline__ void block_partial(double v, int slot, double (*s_red)[4]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_red[w][slot] = v;
+}
+
+template <int PREC, int T>
+__global__ void __launch_bounds__(256) k_eam_bwd1(View V) {
+    __shared__ double s_red[8][4];
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    const int n = V.n_pad;
+    const double rc = V.tab->eam[0], Aem = V.tab->eam[1], rc2 = rc * rc;
+    double rho = 0.0, lam = 0.0;
+    bool valid = false;
+    if (gw * A < n) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            double xi, yi, zi;
+            int ti;
+            load64<PREC>(V, p, xi, yi, zi, ti);
+            const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
+            for_list(V, p, sub, T, [&](uint32_t e) {
+                const int j = entry_j(e);
+                double xj, yj, zj;
+                int tj;
+                load64<PREC>(V, j, xj, yj, zj, tj);
+                const double dx = xi - xj - entry_dx(e) * R.h[0];
+                const double dy = yi - yj - entry_dy(e) * R.h[1];
+                const double dz = zi - zj - entry_dz(e) * R.h[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) return;
+                const double r = sqrt(r2), t = rc - r;
+                rho += t * t;
+                const double w = ((gix - V.gs[j]) * dx + (giy - V.gs[n + j]) * dy + (giz - V.gs[2 * n + j]) * dz) / r;
+                lam += w * (-2.0 * t);
+            });
+        }
+    }
+    rho = tgroup_sum<T>(rho);
+    lam = tgroup_sum<T>(lam);
+    double partA = 0.0;
+    if (valid && sub == 0) {
+        const double sq = rho > 0.0 ? sqrt(rho) : 0.0;
+        const double fp = rho > 0.0 ? -0.5 * Aem / sq : 0.0;
+        const double f2 = rho > 0.0 ? 0.25 * Aem / (rho * sq) : 0.0;
+        const double dA = rho > 0.0 ? -0.5 / sq : 0.0;
+        V.bw[p] = fp;
+        V.bw[n + p] = lam * f2;
+        partA = -lam * dA;
+    }
+    block_partial(partA, 0, s_red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k][0];
+        V.gp_part[(size_t)blockIdx.x * 4] = t;
+    }
+}
+
+template <int PREC, int T>
+__global__ void __launch_bounds__(256) k_eam_bwd2(View V) {
+    __shared__ double s_red[8][4];
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = gw * A + lane / T;
+    const int sub = lane & (T - 1);
+    const int n = V.n_pad;
+    const double rc = V.tab->eam[0], c0 = V.tab->eam[2], c1 = V.tab->eam[3], c2 = V.tab->eam[4];
+    const double rc2 = rc * rc;
+    double gx = 0.0, gy = 0.0, gz = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    bool valid = false;
+    if (gw * A < n) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            double xi, yi, zi;
+            int ti;
+            load64<PREC>(V, p, xi, yi, zi, ti);
+            const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
+            const double fpi = V.bw[p], mui = V.bw[n + p];
+            for_list(V, p, sub, T, [&](uint32_t e) {
+                const int j = entry_j(e);
+                double xj, yj, zj;
+                int tj;
+                load64<PREC>(V, j, xj, yj, zj, tj);
+                const double dx = xi - xj - entry_dx(e) * R.h[0];
+                const double dy = yi - yj - entry_dy(e) * R.h[1];
+                const double dz = zi - zj - entry_dz(e) * R.h[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) return;
+                const double r = sqrt(r2), ir = 1.0 / r, t = rc - r;
+                const double ux = dx * ir, uy = dy * ir, uz = dz * ir;
+                const double Gx = gix - V.gs[j], Gy = giy - V.gs[n + j], Gz = giz - V.gs[2 * n + j];
+                const double w = Gx * ux + Gy * uy + Gz * uz;
+                const double gu = gix * ux + giy * uy + giz * uz;
+                const double P = c0 + r * (c1 + r * c2), dP = c1 + 2.0 * c2 * r;
+                const double dphi = -2.0 * t * P + t * t * dP;
+                const double d2phi = 2.0 * P - 4.0 * t * dP + 2.0 * c2 * t * t;
+                const double fs = fpi + V.bw[j];
+                const double drho = -2.0 * t;
+                const double sv = dphi + fs * drho, kv = d2phi + 2.0 * fs;
+                const double emb = (mui + V.bw[n + j]) * drho;
+                const double a = sv * ir, b = w * (kv - sv * ir) + emb;
+                gx -= a * Gx + b * ux;
+                gy -= a * Gy + b * uy;
+                gz -= a * Gz + b * uz;
+                g0 -= gu * (-2.0 * t);
+                g1 -= gu * (-2.0 * t * r + t * t);
+                g2 -= gu * (-2.0 * t * r * r + 2.0 * r * t * t);
+            });
+        }
+    }
+    gx = tgroup_sum<T>(gx);
+    gy = tgroup_sum<T>(gy);
+    gz = tgroup_sum<T>(gz);
+    if (valid && sub == 0) {
+        V.gx[p] = gx; V.gx[n + p] = gy; V.gx[2 * n + p] = gz;
+    }
+    block_partial(g0, 1, s_red);
+    block_partial(g1, 2, s_red);
+    block_partial(g2, 3, s_red);
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < 4) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k][threadIdx.x];
+        V.gp_part[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
+    }
+}
+
+// block partials in block order -> grad_params {0 (cut-off), A, c0, c1, c2}
+__global__ void k_eam_gp_reduce(View V, int nblocks, double *grad_params) {
+    const int t = threadIdx.x;
+    if (t >= 4) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += V.gp_part[(size_t)b * 4 + t];
+    grad_params[1 + t] = s;
+    if (t == 0) grad_params[0] = 0.0;
+}
+
 __global__ void k_grad_out(View V, double *grad_x) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= V.n_pad) return;
@@ -320,6 +491,35 @@ static const void *pick_bwd(int T) {
         case 16: return (const void *)k_lj_bwd<PREC, 16, NTM>;
         default: return (const void *)k_lj_bwd<PREC, 32, NTM>;
     }
+}
+
+template <int PREC>
+static void pick_eam_bwd(int T, const void **k1, const void **k2) {
+    switch (T) {
+        case 1: *k1 = (const void *)k_eam_bwd1<PREC, 1>; *k2 = (const void *)k_eam_bwd2<PREC, 1>; break;
+        case 2: *k1 = (const void *)k_eam_bwd1<PREC, 2>; *k2 = (const void *)k_eam_bwd2<PREC, 2>; break;
+        case 4: *k1 = (const void *)k_eam_bwd1<PREC, 4>; *k2 = (const void *)k_eam_bwd2<PREC, 4>; break;
+        case 8: *k1 = (const void *)k_eam_bwd1<PREC, 8>; *k2 = (const void *)k_eam_bwd2<PREC, 8>; break;
+        case 16: *k1 = (const void *)k_eam_bwd1<PREC, 16>; *k2 = (const void *)k_eam_bwd2<PREC, 16>; break;
+        default: *k1 = (const void *)k_eam_bwd1<PREC, 32>; *k2 = (const void *)k_eam_bwd2<PREC, 32>; break;
+    }
+}
+
+cudaError_t launch_eam_backward(const View &V, const double *grad_f, double *grad_x, double *grad_params,
+                                int nblocks, cudaStream_t s) {
+    k_grad_in<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, grad_f);
+    const void *k1, *k2;
+    if (V.prec == MD_PREC_FP64) pick_eam_bwd<MD_PREC_FP64>(V.tpa, &k1, &k2);
+    else pick_eam_bwd<MD_PREC_MIXED>(V.tpa, &k1, &k2);
+    View vv = V;
+    void *args[] = {&vv};
+    cudaError_t e = cudaLaunchKernel(k1, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernel(k2, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    if (grad_params) k_eam_gp_reduce<<<1, 32, 0, s>>>(V, nblocks, grad_params);
+    if (grad_x) k_grad_out<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, grad_x);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backward(const View &V, const double *grad_f, double *grad_x, double *grad_params, int nblocks,

@@ -743,18 +743,22 @@ md_status md_set_params(md_system *h, const double *params) {
 
 md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x, double *grad_params) {
     if (!h || !grad_f) return fail(h, MD_ERR_INVALID, "null argument");
-    if (h->cfg.pot != MD_POT_LJ) return fail(h, MD_ERR_UNSUPPORTED, "backward is implemented for LJ");
     if (h->V.half) return fail(h, MD_ERR_UNSUPPORTED, "backward needs a full list (md_set_kernel with MD_LIST_FULL)");
     View &V = h->V;
-    if (!V.gs) {
-        cudaError_t e = dalloc(h, &V.gs, 3 * (size_t)V.n_pad);
-        if (e == cudaSuccess) e = dalloc(h, &V.gx, 3 * (size_t)V.n_pad);
+    const bool eam = h->cfg.pot == MD_POT_EAM_FS;
+    if (!V.gs || (eam && !V.bw)) {
+        cudaError_t e = cudaSuccess;
+        if (!V.gs) {
+            e = dalloc(h, &V.gs, 3 * (size_t)V.n_pad);
+            if (e == cudaSuccess) e = dalloc(h, &V.gx, 3 * (size_t)V.n_pad);
+        }
+        if (e == cudaSuccess && eam) e = dalloc(h, &V.bw, 2 * (size_t)V.n_pad);
         if (e != cudaSuccess) return fail(h, MD_ERR_OOM, "backward buffers: %s", cudaGetErrorString(e));
         drop_graph(h);
     }
     const int nb = backward_partial_blocks(V);
     const int ntm = V.ntypes == 1 ? 1 : (V.ntypes == 2 ? 2 : kMaxTypes);
-    const size_t need = (size_t)nb * 2 * ntm * ntm;
+    const size_t need = eam ? (size_t)nb * 4 : (size_t)nb * 2 * ntm * ntm;
     if (need > h->gp_part_size) {
         dfree(h, V.gp_part);
         V.gp_part = nullptr;
@@ -763,7 +767,8 @@ md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x,
         h->gp_part_size = need;
         drop_graph(h);
     }
-    CK(h, launch_backward(V, grad_f, grad_x, grad_params, nb, h->s));
+    if (eam) CK(h, launch_eam_backward(V, grad_f, grad_x, grad_params, nb, h->s));
+    else CK(h, launch_backward(V, grad_f, grad_x, grad_params, nb, h->s));
     return MD_OK;
 }
 

@@ -129,6 +129,7 @@ struct View {
     double *ev_tile;      // [n_tiles][8] per-tile partial sums
     // backward
     double *gs, *gx;      // [3][n_pad] gradient in / out (sorted)
+    double *bw;           // [2][n_pad] EAM backward: F'(rho_i), mu_i = lambda_i F''(rho_i)
     double *gp_part;      // per block partial parameter gradients
     const PairTab *tab;
     Ctl *ctl;

@@ -44,6 +44,8 @@ cudaError_t launch_state_out(const View &V, double *x, double *v, double *f, cud
 cudaError_t launch_ev_reduce(const View &V, double *out, cudaStream_t s);
 cudaError_t launch_backward(const View &V, const double *grad_f, double *grad_x, double *grad_params,
                             int nblocks_part, cudaStream_t s);
+cudaError_t launch_eam_backward(const View &V, const double *grad_f, double *grad_x, double *grad_params,
+                                int nblocks_part, cudaStream_t s);
 cudaError_t launch_neighbors_out(const View &V, int *counts, int *nbr, int cap, cudaStream_t s);
 int backward_partial_blocks(const View &V);
 

@@ -212,10 +212,12 @@ class System:
         self._call("md_set_params", p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
     def backward(self, grad_f):
-        """dL/dx (n,3) and dL/dparams (2 n_types^2, ABI layout) for dL/dF = grad_f."""
+        """dL/dx (n,3) and dL/dparams (ABI layout: 2 n_types^2 for LJ; 5 for EAM, the cut-off slot 0)
+        for dL/dF = grad_f."""
         g = _dev(grad_f, torch.float64, (-1, 3))
         gx = torch.empty_like(g)
-        gp = torch.empty(2 * self.n_types * self.n_types, dtype=torch.float64, device="cuda")
+        npar = 5 if self.potential == "eam" else 2 * self.n_types * self.n_types
+        gp = torch.empty(npar, dtype=torch.float64, device="cuda")
         self._call("md_forces_backward", _ptr(g), _ptr(gx), _ptr(gp))
         return gx, gp
 
@@ -313,3 +315,36 @@ class LJForces(torch.autograd.Function):
         gs_t = torch.as_tensor(gs, dtype=sdt, device=sdev)
         gxo = gx.to(ctx.x_dtype) if ctx.has_x else None
         return None, gxo, ge_t, gs_t
+
+
+class EAMForces(torch.autograd.Function):
+    """F = EAMForces.apply(system, x, params) for an EAM system.
+
+    params: (5,) tensor (rc, A, c0, c1, c2), any float dtype, learnable; the
+    cut-off entry must stay at the system's cut-off and receives a zero
+    gradient.  x (n,3) may be None to keep the system's positions.  Forward
+    sets the parameters (and positions), runs the density and force kernels;
+    backward runs the library's two-pass EAM backward kernels.
+    """
+
+    @staticmethod
+    def forward(ctx, system, x, params):
+        if system.potential != "eam":
+            raise MDError(int(L.MD_ERR_INVALID), "EAMForces needs an EAM system")
+        system.set_params(params.detach().cpu().double().numpy())
+        if x is not None:
+            system.set_state(x=x.detach())
+        f = system.compute_forces()
+        ctx.system = system
+        ctx.has_x = x is not None
+        ctx.x_dtype = x.dtype if x is not None else None
+        ctx.p_dtype = (params.dtype, params.device)
+        return f
+
+    @staticmethod
+    def backward(ctx, grad_f):
+        gx, gp = ctx.system.backward(grad_f.contiguous())
+        pdt, pdev = ctx.p_dtype
+        gxo = gx.to(ctx.x_dtype) if ctx.has_x else None
+        return None, gxo, gp.to(dtype=pdt, device=pdev)
+

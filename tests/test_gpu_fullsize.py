@@ -91,3 +91,39 @@ def test_eam500k_mixed_and_fp64():
                         ftm2v=d["ftm2v"], precision=prec, tpa=4) as s:
             f = s.compute_forces().cpu().numpy()
         assert rel_maxnorm(f[idx], fr) < tol, prec
+
+
+def test_eam500k_backward_directional_fd():
+    # property at full size: grad_x . delta and dL/dA equal central differences of
+    # L = sum g.F computed with the FP64 forward (which is parity-checked above)
+    import torch
+    from paper_1009_4330_gb300 import System
+    d = synth.config2(displacement=0.1)
+    x, box = d["x"], d["box"]
+    rng = np.random.default_rng(17)
+    g = rng.standard_normal(x.shape)
+    # direction supported on sampled atoms none of whose pairs lies within 1e-4
+    # of rc: the force derivatives jump there, and only the moved atoms' pairs move
+    idx = [i for i in sample(x.shape[0], 300, seed=23) if oracle.min_gap(x, box, d["rc"], [i]) > 1e-4]
+    assert len(idx) > 250
+    delta = np.zeros_like(x)
+    delta[idx] = rng.standard_normal((len(idx), 3))
+    gt = torch.tensor(g, device="cuda")
+    with System.eam(x, d["v"], box, eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
+                    ftm2v=d["ftm2v"], precision="fp64", tpa=4) as s:
+        gx, gp = s.backward(g)
+        gdx = float((gx.cpu().numpy() * delta).sum())
+        h = 1e-6
+        lp = []
+        for sgn in (1, -1):
+            s.set_state(x=torch.tensor(x + sgn * h * delta, device="cuda"))
+            lp.append(float((s.compute_forces() * gt).sum()))
+        s.set_state(x=torch.tensor(x, device="cuda"))
+        la = []
+        for sgn in (1, -1):
+            p = np.array(d["eam"], dtype=np.float64)
+            p[1] += sgn * h
+            s.set_params(p)
+            la.append(float((s.compute_forces() * gt).sum()))
+    assert gdx == pytest.approx((lp[0] - lp[1]) / (2 * h), rel=1e-5)
+    assert gp.cpu().numpy()[1] == pytest.approx((la[0] - la[1]) / (2 * h), rel=1e-5)
