@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--vec", type=int, default=0, help="list entries per thread per load (0: default for tpa)")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
+    ap.add_argument("--profile", default=None, choices=["build", "eam_backward"],
+                    help="run one small workload for a profiler and exit: 'build' = LJ liquid (--cells, --rc), "
+                         "100 steps to melt the lattice, then two list rebuilds; 'eam_backward' = EAM metal "
+                         "(--cells), forces + backward twice")
+    ap.add_argument("--rc", type=float, default=2.5, help="LJ cut-off of --profile build")
     return ap.parse_args()
 
 
@@ -461,9 +466,35 @@ def eam_backward_timing(synth, reps=10):
     return out
 
 
+def run_profile(args):
+    """Small workloads for profiler captures (not a bench line)."""
+    import torch
+    import synth
+    from paper_1009_4330_gb300 import System
+    if args.profile == "build":
+        s, d = make_lj(synth, args.cells, args.rc, "mixed", tpa=args.tpa or (1 if args.rc < 3 else 4), lst="full")
+        s.step(100)
+        s.build_neighbors()
+        s.build_neighbors()
+    else:
+        d = synth.config2(cells=args.cells, displacement=0.1)
+        s = System.eam(d["x"], d["v"], d["box"], eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
+                       ftm2v=d["ftm2v"], precision="mixed", tpa=args.tpa or 1)
+        g = torch.ones((d["x"].shape[0], 3), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            s.compute_forces()
+            s.backward(g)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "atoms": int(d["x"].shape[0]), "info": s.info()}))
+    s.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

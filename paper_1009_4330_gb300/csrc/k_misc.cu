@@ -313,10 +313,11 @@ __global__ void __launch_bounds__(256) k_eam_bwd1(View V) {
                 const double dz = zi - zj - entry_dz(e) * R.h[2];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rc2)) return;
-                const double r = sqrt(r2), t = rc - r;
+                const double ir = rsqrt_newton(r2), r = r2 * ir, t = rc - r;
                 rho += t * t;
-                const double w = ((gix - V.gs[j]) * dx + (giy - V.gs[n + j]) * dy + (giz - V.gs[2 * n + j]) * dz) / r;
-                lam += w * (-2.0 * t);
+                // w rho'(r) with w = (g_i - g_j).d / r and rho' = -2 (rc - r)
+                const double Gd = (gix - V.gs[j]) * dx + (giy - V.gs[n + j]) * dy + (giz - V.gs[2 * n + j]) * dz;
+                lam -= 2.0 * t * ir * Gd;
             });
         }
     }
@@ -373,25 +374,26 @@ __global__ void __launch_bounds__(256) k_eam_bwd2(View V) {
                 const double dz = zi - zj - entry_dz(e) * R.h[2];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rc2)) return;
-                const double r = sqrt(r2), ir = 1.0 / r, t = rc - r;
-                const double ux = dx * ir, uy = dy * ir, uz = dz * ir;
+                const double ir = rsqrt_newton(r2), r = r2 * ir, t = rc - r;
                 const double Gx = gix - V.gs[j], Gy = giy - V.gs[n + j], Gz = giz - V.gs[2 * n + j];
-                const double w = Gx * ux + Gy * uy + Gz * uz;
-                const double gu = gix * ux + giy * uy + giz * uz;
+                const double w = (Gx * dx + Gy * dy + Gz * dz) * ir;     // G.u
+                const double gu = (gix * dx + giy * dy + giz * dz) * ir;  // g_i.u
                 const double P = c0 + r * (c1 + r * c2), dP = c1 + 2.0 * c2 * r;
-                const double dphi = -2.0 * t * P + t * t * dP;
+                const double dphi = t * (t * dP - 2.0 * P);
                 const double d2phi = 2.0 * P - 4.0 * t * dP + 2.0 * c2 * t * t;
                 const double fs = fpi + V.bw[j];
                 const double drho = -2.0 * t;
                 const double sv = dphi + fs * drho, kv = d2phi + 2.0 * fs;
                 const double emb = (mui + V.bw[n + j]) * drho;
-                const double a = sv * ir, b = w * (kv - sv * ir) + emb;
-                gx -= a * Gx + b * ux;
-                gy -= a * Gy + b * uy;
-                gz -= a * Gz + b * uz;
-                g0 -= gu * (-2.0 * t);
-                g1 -= gu * (-2.0 * t * r + t * t);
-                g2 -= gu * (-2.0 * t * r * r + 2.0 * r * t * t);
+                // -(s/r) G - (w (k - s/r) + emb) u, with u = d / r
+                const double a = sv * ir, b = (w * (kv - a) + emb) * ir;
+                gx -= a * Gx + b * dx;
+                gy -= a * Gy + b * dy;
+                gz -= a * Gz + b * dz;
+                // -(g_i.u) dphi'/dc_q: dphi'/dc = (-2t, t (t - 2r), 2 r t (t - r))
+                g0 += 2.0 * gu * t;
+                g1 -= gu * t * (t - 2.0 * r);
+                g2 -= 2.0 * gu * r * t * (t - r);
             });
         }
     }

@@ -316,19 +316,20 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 // the list equals the FP64 definition exactly.  HALF keeps j > i only.
 constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
 constexpr int kBatch = 14;  // rounds whose list entries are appended together
+constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
 
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
-    __shared__ float4 s_h[8][32];
-    __shared__ float4 s_q[8][kQueue];  // shifted candidate position, .w = list entry bits
-    __shared__ float4 s_box[8][2];     // bounding box of the home chunk: lo, hi
-    __shared__ int2 s_cell[8][27];     // neighbour cells: first slot, count
-    __shared__ uint32_t s_st[8][4][32];  // per home atom: its open group of 4 entries
-    __shared__ uint32_t s_t[8][kBatch][32];  // per round: home atom's mask of accepted candidates
-    __shared__ uint32_t s_e[8][kBatch][32];  // per round: candidate's list entry
+__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(View V, KArgs a) {
+    __shared__ float4 s_h[kBuildWarps][32];
+    __shared__ float4 s_q[kBuildWarps][kQueue];  // shifted candidate position, .w = list entry bits
+    __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
+    __shared__ int2 s_cell[kBuildWarps][27];     // neighbour cells: first slot, count
+    __shared__ uint32_t s_st[kBuildWarps][4][32];  // per home atom: its open group of 4 entries
+    __shared__ uint32_t s_t[kBuildWarps][kBatch][32];  // per round: home atom's mask of accepted candidates
+    __shared__ uint32_t s_e[kBuildWarps][kBatch][32];  // per round: candidate's list entry
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
-    const int gw = blockIdx.x * 8 + w;
+    const int gw = blockIdx.x * kBuildWarps + w;
     const int gb = gw / V.hsplit, part = gw - gb * V.hsplit;
     int my_max = 0;
     long long my_sum = 0;
@@ -554,8 +555,8 @@ __global__ void __launch_bounds__(256, 4) k_build(View V, KArgs a) {
     }
     // statistics per replica: warp max / sum, merged over the block's warps
     // that belong to the same replica, one atomic per run
-    __shared__ int s_max[8], s_rep[8];
-    __shared__ long long s_sum[8];
+    __shared__ int s_max[kBuildWarps], s_rep[kBuildWarps];
+    __shared__ long long s_sum[kBuildWarps];
     for (int o = 16; o > 0; o >>= 1) {
         my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
         my_sum += __shfl_xor_sync(0xffffffffu, my_sum, o);
@@ -614,7 +615,7 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
         kb = V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>;
     else
         kb = V.half ? (const void *)k_build<MD_PREC_MIXED, 1> : (const void *)k_build<MD_PREC_MIXED, 0>;
-    seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + 7) / 8), dim3(256), 0, a});
+    seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + kBuildWarps - 1) / kBuildWarps), dim3(32 * kBuildWarps), 0, a});
 }
 
 }  // namespace md
