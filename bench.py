@@ -303,7 +303,7 @@ def run_ours(args, ws, rank, local):
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
     # our kernels in the timed region: loop control once, per step the drift and
     # the force pass (1 kernel full list, 3 half list), 8 per list rebuild
-    launches = 1 + K * (1 + (3 if i1["list"] == "half" else 1)) + 8 * rebuilds
+    launches = 1 + K * (1 + (3 if i1["list"] == "half" else 1)) + (9 if i1["tile_atoms"] else 8) * rebuilds
     # dominant kernel: the force pass as md_step runs it, timed with CUDA events on the handle's stream
     f_ms, f_bytes = s.time_force(warmup=3, reps=20)
     # the ceiling of the same access pattern: the force pass's memory-only twin
@@ -359,6 +359,20 @@ def side_runs(synth, cells, K, W):
     ms, i0, i1, _ = time_steps(s, k, 3)
     n = d["x"].shape[0]
     out["fp64_rc2.5"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"]}
+    s.close()
+    # design alternative: block-local lists with shared-memory staging (off by
+    # default), force pass and its memory-only twin against the default layout
+    s, d = make_lj(synth, cells, 2.5, "mixed", tpa=1, lst="full")
+    s.step(20)
+    alt = {}
+    for staged in (False, True):
+        s.set_staging(staged)
+        fms, fby = s.time_force(3, 10)
+        gms = s.time_gather(3, 10)
+        inf = s.info()
+        alt["staged" if staged else "gathered"] = {"force_ms": fms, "twin_ms": gms, "tiles_staged": inf["tiles_staged"],
+                                                   "n_tiles": inf["n_tiles_force"], "block": inf["block"]}
+    out["staging_alternative_rc2.5"] = alt
     s.close()
     # rc 5.0, mixed
     s, d = make_lj(synth, cells, 5.0, "mixed", tpa=0)

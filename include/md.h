@@ -197,6 +197,21 @@ md_status md_autotune(md_system *h, const char *cache_path);
 md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block, int32_t vec);
 
 /*
+ * Block-local lists with shared-memory staging (off by default; a measured
+ * design alternative to gathering neighbour records through L1).  When on,
+ * for mixed precision with a full list and force blocks of 32..128 atoms,
+ * each force block stages the records of every cell within one cell of its
+ * atoms' cells in shared memory (up to 2048 records) and its atoms' list
+ * entries hold offsets into that staging; a block whose cells do not fit
+ * keeps slot entries.  md_info reports tile_atoms / tiles_staged.  Forces,
+ * lists (md_get_neighbors) and gradients are the same either way; on GB300
+ * at the LJ-liquid densities the staged passes measured slower (shared-memory
+ * bank conflicts of the scattered record reads, and the staging itself).
+ * Rebuilds the lists when the layout changes.
+ */
+md_status md_set_staging(md_system *h, int32_t on);
+
+/*
  * md_step without CUDA graphs: the step's kernels are launched one by one
  * and the list-rebuild kernels every step (each returns at once for replicas
  * whose displacement check did not ask for a rebuild).  Same results as
@@ -219,6 +234,9 @@ typedef struct {
     int64_t rebuilds;        /* list builds since creation                                */
     int64_t steps;           /* time steps taken since creation                           */
     int32_t bins[3];         /* bins per axis (replica 0)                                 */
+    int32_t tile_atoms;      /* atoms per force block with block-local lists, 0 = none    */
+    int32_t tiles_staged;    /* force blocks whose records are staged (of n_tiles_force)  */
+    int32_t n_tiles_force;   /* force blocks (tiles) of the last build                    */
 } md_info_t;
 
 /*

@@ -19,7 +19,7 @@ MD_MAX_TYPES = 8
 EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "md_compute_forces", "md_step",
            "md_energy_virial", "md_get_state", "md_set_state", "md_set_params", "md_forces_backward",
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
-           "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather")
+           "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather", "md_set_staging")
 
 
 class MdConfig(ctypes.Structure):
@@ -35,7 +35,8 @@ class MdInfo(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("n_rep", ctypes.c_int32), ("tpa", ctypes.c_int32),
                 ("list", ctypes.c_int32), ("block", ctypes.c_int32), ("maxneigh", ctypes.c_int32),
                 ("vec", ctypes.c_int32), ("max_count", ctypes.c_int32), ("list_entries", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
-                ("steps", ctypes.c_int64), ("bins", ctypes.c_int32 * 3)]
+                ("steps", ctypes.c_int64), ("bins", ctypes.c_int32 * 3), ("tile_atoms", ctypes.c_int32),
+                ("tiles_staged", ctypes.c_int32), ("n_tiles_force", ctypes.c_int32)]
 
 
 _lib = None

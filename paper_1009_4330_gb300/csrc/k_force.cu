@@ -116,11 +116,14 @@ __device__ __forceinline__ double group_sum(double x) {
 // terms of one round (at most Q) are summed plainly and the round's sum is
 // added to the running total with compensation (blocked Kahan summation:
 // error ~ (Q + 2) u sum |terms| instead of ~n u for n plain additions).
-template <int PREC, int T, int Q, class Pair>
+// LOCAL: the entries are block-local and the records come from the block's
+// staging in shared memory (srec; mixed precision only).
+template <int PREC, int T, int Q, bool LOCAL, class Pair>
 __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int sub, int cnt,
                                           typename Pol<PREC>::real xi, typename Pol<PREC>::real yi,
                                           typename Pol<PREC>::real zi, typename Pol<PREC>::real hx,
-                                          typename Pol<PREC>::real hy, typename Pol<PREC>::real hz, Pair &pair) {
+                                          typename Pol<PREC>::real hy, typename Pol<PREC>::real hz,
+                                          const float4 *srec, Pair &pair) {
     using P = Pol<PREC>;
     using real = typename P::real;
     constexpr int PER = T * Q;
@@ -135,7 +138,14 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
         int tj[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            if (q < left) P::load(V, entry_j(cur[q]), xj[q], yj[q], zj[q], tj[q]);
+            if (q < left) {
+                if constexpr (LOCAL) {
+                    const float4 r4 = srec[entry_j(cur[q]) & (kTileCap - 1)];
+                    xj[q] = r4.x; yj[q] = r4.y; zj[q] = r4.z; tj[q] = __float_as_int(r4.w);
+                } else {
+                    P::load(V, entry_j(cur[q]), xj[q], yj[q], zj[q], tj[q]);
+                }
+            }
         }
         pair.round_begin();
 #pragma unroll
@@ -153,6 +163,32 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
 #pragma unroll
         for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
     }
+}
+
+// the list walk in this block's tile mode (records staged or gathered)
+template <int PREC, int T, int Q, class Pair>
+__device__ __forceinline__ void walk_mode(const View &V, int mode, const uint32_t *lp, int sub, int cnt,
+                                          typename Pol<PREC>::real xi, typename Pol<PREC>::real yi,
+                                          typename Pol<PREC>::real zi, const Rep &R, const float4 *srec,
+                                          Pair &pair) {
+    using P = Pol<PREC>;
+    if constexpr (PREC == MD_PREC_MIXED) {
+        if (mode == 1) {
+            walk_list<PREC, T, Q, true>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), srec, pair);
+            return;
+        }
+    }
+    walk_list<PREC, T, Q, false>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), srec, pair);
+}
+
+// stage the block's tile when its entries are block-local (before the
+// kernel's first block barrier)
+template <int PREC>
+__device__ __forceinline__ int begin_tile(const View &V, int T, float4 *srec) {
+    if constexpr (PREC != MD_PREC_MIXED) return 0;
+    const int mode = tile_mode(V, T);
+    if (mode == 1) stage_tile(V, blockIdx.x, srec);
+    return mode;
 }
 
 // Epilogue of atom p (after the group reduction), by the group's lane 0.
@@ -264,6 +300,8 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
         }
     }
     if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    extern __shared__ float4 s_rec[];
+    const int tmode = HALF ? 0 : begin_tile<PREC>(V, T, s_rec);
     __syncthreads();
 
     const unsigned err = V.ctl->err;
@@ -273,7 +311,7 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int p = gw * A + lane / T;
     const int sub = lane & (T - 1);
-    const bool warp_in = (gw * A < V.n_pad) && err == 0;
+    const bool warp_in = (gw * A < V.n_pad) && err == 0 && tmode >= 0;
 
     LJPair<PREC, MT, HALF, EV> pr;
     pr.V = &V;
@@ -293,7 +331,7 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
             real xi, yi, zi;
             P::load(V, p, xi, yi, zi, pr.ti);
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
-            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
+            walk_mode<PREC, T, Q>(V, tmode, lp, sub, cnt, xi, yi, zi, R, s_rec, pr);
         }
     }
     const double fx = group_sum<T>(pr.ax.value());
@@ -336,6 +374,9 @@ struct GatherPair {
 template <int T, int Q>
 __global__ void __launch_bounds__(256, 4) k_gather_probe(View V, KArgs a) {
     using P = Pol<MD_PREC_MIXED>;
+    extern __shared__ float4 s_rec[];
+    const int tmode = begin_tile<MD_PREC_MIXED>(V, T, s_rec);
+    __syncthreads();
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -344,7 +385,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_probe(View V, KArgs a) {
     GatherPair pr;
     pr.acc = 0.f;
     bool valid = false;
-    if (gw * A < V.n_pad) {
+    if (gw * A < V.n_pad && tmode >= 0) {
         const Rep &R = V.rep[V.tile_rep[p >> 5]];
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
@@ -353,7 +394,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_probe(View V, KArgs a) {
             int ti;
             P::load(V, p, xi, yi, zi, ti);
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
-            walk_list<MD_PREC_MIXED, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
+            walk_mode<MD_PREC_MIXED, T, Q>(V, tmode, lp, sub, cnt, xi, yi, zi, R, s_rec, pr);
         }
     }
     const double sum = group_sum<T>((double)pr.acc);
@@ -382,7 +423,8 @@ void gather_probe_sequence(const View &V, int block, std::vector<KCall> &seq) {
     KArgs a{};
     const long long threads = (long long)V.n_pad * V.tpa;
     const void *fn = V.vec == 4 ? pick_probe_q<4>(V.tpa) : (V.vec == 2 ? pick_probe_q<2>(V.tpa) : pick_probe_q<1>(V.tpa));
-    seq.push_back(KCall{fn, dim3((unsigned)((threads + block - 1) / block)), dim3(block), 0, a});
+    const size_t sm = V.tile_atoms > 0 ? kTileSmem : 0;
+    seq.push_back(KCall{fn, dim3((unsigned)((threads + block - 1) / block)), dim3(block), sm, a});
 }
 
 // zero F before a half-list pass
@@ -446,6 +488,9 @@ template <int PREC, int T, int Q>
 __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
+    extern __shared__ float4 s_rec[];
+    const int tmode = begin_tile<PREC>(V, T, s_rec);
+    __syncthreads();
     const unsigned err = V.ctl->err;
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31;
@@ -457,7 +502,7 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     pr.rc = (PREC == MD_PREC_FP64) ? (real)V.tab->eam[0] : (real)V.tab->eamf[0];
     pr.rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
     bool valid = false;
-    if (gw * A < V.n_pad && err == 0) {
+    if (gw * A < V.n_pad && err == 0 && tmode >= 0) {
         const Rep &R = V.rep[V.tile_rep[p >> 5]];
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
@@ -466,7 +511,7 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
             int ti;
             P::load(V, p, xi, yi, zi, ti);
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
-            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
+            walk_mode<PREC, T, Q>(V, tmode, lp, sub, cnt, xi, yi, zi, R, s_rec, pr);
         }
     }
     const double rho = group_sum<T>(pr.acc.value());
@@ -526,6 +571,8 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
     using real = typename P::real;
     __shared__ double s_ftm[kMaxTypes];
     if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    extern __shared__ float4 s_rec[];
+    const int tmode = begin_tile<PREC>(V, T, s_rec);
     __syncthreads();
     const unsigned err = V.ctl->err;
     const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
@@ -547,7 +594,7 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
     for (int k = 0; k < 6; ++k) pr.w[k].zero();
     bool valid = false;
     int ti = 0;
-    if (gw * A < V.n_pad && err == 0) {
+    if (gw * A < V.n_pad && err == 0 && tmode >= 0) {
         const Rep &R = V.rep[V.tile_rep[p >> 5]];
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
@@ -556,7 +603,7 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
             P::load(V, p, xi, yi, zi, ti);
             pr.fpi = (PREC == MD_PREC_FP64) ? P::fp(V, p) : (real)__int_as_float(ti);
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
-            walk_list<PREC, T, Q>(V, lp, sub, cnt, xi, yi, zi, P::h(R, 0), P::h(R, 1), P::h(R, 2), pr);
+            walk_mode<PREC, T, Q>(V, tmode, lp, sub, cnt, xi, yi, zi, R, s_rec, pr);
         }
     }
     const double fx = group_sum<T>(pr.ax.value());
@@ -772,6 +819,7 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
     const long long threads = (long long)V.n_pad * T;
     const dim3 grid((unsigned)((threads + block - 1) / block));
     const int fp64 = (V.prec == MD_PREC_FP64);
+    const size_t sm = V.tile_atoms > 0 ? kTileSmem : 0;
     if (V.pot == MD_POT_LJ) {
         const int mt = V.ntypes > 1 ? 1 : 0;
         const void *fn = fp64 ? pick_lj_prec<MD_PREC_FP64>(T, V.vec, V.half, ev, mt)
@@ -784,15 +832,15 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
             seq.push_back(KCall{fn, grid, dim3(block), 0, af});
             seq.push_back(KCall{(const void *)k_kick, dim3((V.n_pad + 255) / 256), dim3(256), 0, a});
         } else {
-            seq.push_back(KCall{fn, grid, dim3(block), 0, a});
+            seq.push_back(KCall{fn, grid, dim3(block), sm, a});
         }
     } else {
         KArgs ar = a;
         ar.in_graph = 0;
         const void *fr = fp64 ? pick_rho<MD_PREC_FP64>(T, V.vec) : pick_rho<MD_PREC_MIXED>(T, V.vec);
-        seq.push_back(KCall{fr, grid, dim3(block), 0, ar});
+        seq.push_back(KCall{fr, grid, dim3(block), sm, ar});
         const void *fn = fp64 ? pick_eamf<MD_PREC_FP64>(T, V.vec, ev) : pick_eamf<MD_PREC_MIXED>(T, V.vec, ev);
-        seq.push_back(KCall{fn, grid, dim3(block), 0, a});
+        seq.push_back(KCall{fn, grid, dim3(block), sm, a});
     }
 }
 

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_lj_bwd(View V, KArgs a) {
             for (int k0 = sub * Q; k0 < cnt; k0 += T * Q) {
                 for (int k = k0; k < k0 + Q && k < cnt; ++k) {
                     const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, maxn)];
-                    const int j = entry_j(e);
+                    const int j = entry_slot(V, p, e);
                     double xj, yj, zj;
                     int tj;
                     load64<PREC>(V, j, xj, yj, zj, tj);
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_eam_bwd1(View V) {
             load64<PREC>(V, p, xi, yi, zi, ti);
             const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
             for_list(V, p, sub, T, [&](uint32_t e) {
-                const int j = entry_j(e);
+                const int j = entry_slot(V, p, e);
                 double xj, yj, zj;
                 int tj;
                 load64<PREC>(V, j, xj, yj, zj, tj);
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256) k_eam_bwd2(View V) {
             const double gix = V.gs[p], giy = V.gs[n + p], giz = V.gs[2 * n + p];
             const double fpi = V.bw[p], mui = V.bw[n + p];
             for_list(V, p, sub, T, [&](uint32_t e) {
-                const int j = entry_j(e);
+                const int j = entry_slot(V, p, e);
                 double xj, yj, zj;
                 int tj;
                 load64<PREC>(V, j, xj, yj, zj, tj);
@@ -446,7 +446,7 @@ __global__ void k_neighbors_out(View V, int *counts, int *nbr, int cap) {
     counts[o] = c;
     for (int k = 0; k < c && k < cap; ++k) {
         const uint32_t e = V.nlist[list_index(p, k, V.ltpa, V.lvec, V.maxneigh)];
-        nbr[o * cap + k] = V.id[entry_j(e)];
+        nbr[o * cap + k] = V.id[entry_slot(V, p, e)];
     }
 }
 

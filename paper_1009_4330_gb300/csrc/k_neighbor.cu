@@ -256,6 +256,153 @@ __global__ void k_gather(View V, KArgs a) {
     V.recb[dst] = rr;
 }
 
+// global bin of slot p (after the gather)
+__device__ __forceinline__ int slot_bin(const View &V, const Rep &R, int p) {
+    const int k = V.bpk[p];
+    return V.lin2bin[R.bin0 + (unpack_bz(k) * R.nb[1] + unpack_by(k)) * R.nb[0] + unpack_bx(k)];
+}
+
+// Per tile of tile_atoms slots (one warp each): the cells of its atoms (a
+// contiguous range of bins, <= 32), their 27-cell neighbourhoods marked in a
+// bitmap over the dilated bounding box (<= kTileBox cells, unwrapped
+// coordinates, so a cell reached through two periodic images is staged
+// twice), the marked cells in box order with their record counts, and the
+// running offsets.  A tile that straddles replicas, spans too many cells or
+// stages more than kTileCap records keeps slot entries (tile_cnt = -1).
+__global__ void __launch_bounds__(128) k_tiles(View V, KArgs a) {
+    __shared__ unsigned s_bits[4][32];
+    __shared__ int s_cnt[4][kTileCells];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * 4 + w;
+    if (t >= V.n_ftiles) return;
+    const int p0 = t * V.tile_atoms;
+    const int p1 = min(p0 + V.tile_atoms, V.n_pad) - 1;
+    const int r = V.tile_rep[p0 >> 5], r1 = V.tile_rep[p1 >> 5];
+    if (!(a.all || V.rep_flag[r] || V.rep_flag[r1])) return;  // lists of this tile unchanged
+    const Rep &R = V.rep[r];
+    int ok = (r == r1);
+    const int pl = min(p1, R.atom0 + R.natoms - 1);
+    if (ok && pl < p0) {  // no real atom
+        if (lane == 0) { V.tile_cnt[t] = 0; V.tile_ncell[t] = 0; }
+        return;
+    }
+    int gb0 = 0, nh = 0;
+    if (ok) {
+        gb0 = slot_bin(V, R, p0);
+        nh = slot_bin(V, R, pl) - gb0 + 1;
+        ok = (nh >= 1 && nh <= 32);
+    }
+    if (!ok) {
+        if (lane == 0) { V.tile_cnt[t] = -1; V.tile_ncell[t] = 0; }
+        return;
+    }
+    const bool act = lane < nh;
+    int bx = 0, by = 0, bz = 0;
+    if (act) {
+        const int xyz = V.bin2xyz[gb0 + lane];
+        bx = unpack_bx(xyz); by = unpack_by(xyz); bz = unpack_bz(xyz);
+    }
+    const int lox = __reduce_min_sync(0xffffffffu, act ? bx : 0x7fffffff) - 1;
+    const int loy = __reduce_min_sync(0xffffffffu, act ? by : 0x7fffffff) - 1;
+    const int loz = __reduce_min_sync(0xffffffffu, act ? bz : 0x7fffffff) - 1;
+    const int dx = __reduce_max_sync(0xffffffffu, act ? bx : -0x7fffffff) - lox + 2;
+    const int dy = __reduce_max_sync(0xffffffffu, act ? by : -0x7fffffff) - loy + 2;
+    const int dz = __reduce_max_sync(0xffffffffu, act ? bz : -0x7fffffff) - loz + 2;
+    ok = dx * dy * dz <= kTileBox;  // each dim <= 1026 (bins per axis <= 1024): no overflow
+    s_bits[w][lane] = 0u;
+    __syncwarp();
+    if (ok && act) {
+        for (int k = 0; k < 27; ++k) {
+            const int row = k / 3;
+            const int ox = k - 3 * row - 1, oy = row % 3 - 1, oz = row / 3 - 1;
+            const int idx = (bx + ox - lox) + dx * ((by + oy - loy) + dy * (bz + oz - loz));
+            atomicOr(&s_bits[w][idx >> 5], 1u << (idx & 31));
+        }
+    }
+    __syncwarp();
+    const unsigned word = ok ? s_bits[w][lane] : 0u;
+    int incl = __popc(word);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const int excl = incl - __popc(word);
+    const int ncell = __shfl_sync(0xffffffffu, incl, 31);
+    ok = ok && ncell <= kTileCells;
+    if (!ok) {
+        if (lane == 0) { V.tile_cnt[t] = -1; V.tile_ncell[t] = 0; }
+        return;
+    }
+    V.tile_bits[(size_t)t * 32 + lane] = word;
+    V.tile_wpre[(size_t)t * 32 + lane] = excl;
+    // the union's cells in box order (coordinates only), then four per lane:
+    // bin, first slot, count (independent loads)
+    unsigned wd = word;
+    int k = excl;
+    while (wd) {
+        s_cnt[w][k++] = lane * 32 + __ffs(wd) - 1;  // box index for now
+        wd &= wd - 1u;
+    }
+    __syncwarp();
+    const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
+    int gbq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int kk = lane + 32 * q;
+        gbq[q] = -1;
+        if (kk < ncell) {
+            const int idx = s_cnt[w][kk];
+            int cx = lox + idx % dx, cy = loy + (idx / dx) % dy, cz = loz + idx / (dx * dy);
+            cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
+            cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
+            cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
+            gbq[q] = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
+        }
+    }
+    int cq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int kk = lane + 32 * q;
+        cq[q] = 0;
+        if (gbq[q] >= 0) {
+            V.tile_first[(size_t)t * kTileCells + kk] = V.bin_start[gbq[q]];
+            cq[q] = V.bin_count[gbq[q]];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (gbq[q] >= 0) s_cnt[w][lane + 32 * q] = cq[q];
+    __syncwarp();
+    // running offsets, four cells per lane
+    int c4[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int kk = 4 * lane + q;
+        c4[q] = kk < ncell ? s_cnt[w][kk] : 0;
+        sum += c4[q];
+    }
+    int run = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, run, o);
+        if (lane >= o) run += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, run, 31);
+    run -= sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int kk = 4 * lane + q;
+        if (kk < ncell) V.tile_off[(size_t)t * kTileCells + kk] = run;
+        run += c4[q];
+    }
+    if (lane == 0) {
+        const bool fits = total <= kTileCap;
+        V.tile_cnt[t] = fits ? total : -1;
+        V.tile_ncell[t] = fits ? ncell : 0;
+        V.tile_box[t] = make_int4(lox, loy, loz, dx | (dy << 16));
+    }
+}
+
 // Exact FP64 list test for a pair inside the FP32 margin band (rare; kept
 // out of line so that it does not cost the main loop registers).
 template <int PREC>
@@ -325,6 +472,7 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
     __shared__ int2 s_cell[kBuildWarps][27];     // neighbour cells: first slot, count
     __shared__ uint32_t s_st[kBuildWarps][4][32];  // per home atom: its open group of 4 entries
+    __shared__ int s_delta[kBuildWarps][2][64];     // per tile of the chunk, per stencil code: entry shift
     __shared__ uint32_t s_t[kBuildWarps][kBatch][32];  // per round: home atom's mask of accepted candidates
     __shared__ uint32_t s_e[kBuildWarps][kBatch][32];  // per round: candidate's list entry
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -390,9 +538,37 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                         s_box[w][1] = make_float4(hix, hiy, hiz, 0.f);
                     }
                 }
+                // Block-local entries: the chunk's atoms lie in one or two tiles; for
+                // each, stencil cell k's records start at tile_off[k] in the tile's
+                // staging, so a candidate's entry j<<6|code becomes
+                // (j - cell start + tile_off[k])<<6|code: a shift per (tile, code).
+                const int tpa_atoms = V.tile_atoms;
+                const int tA = tpa_atoms ? hbase / tpa_atoms : 0;
+                const int tB = tpa_atoms ? (hbase + nh - 1) / tpa_atoms : 0;
+                if (lane < 27) {
+                    const int row = lane / 3;
+                    const int ox = lane - 3 * row - 1, oy = row % 3 - 1, oz = row / 3 - 1;
+                    const int code = ((oz + 1) << 4) | ((oy + 1) << 2) | (ox + 1);
+                    for (int X = 0; X < 2; ++X) {
+                        int delta = 0;
+                        const int t = X ? tB : tA;
+                        if (tpa_atoms && V.tile_cnt[t] >= 0) {
+                            const int4 b = V.tile_box[t];
+                            const int bdx = b.w & 0xffff, bdy = b.w >> 16;
+                            int idx = (bx + ox - b.x) + bdx * ((by + oy - b.y) + bdy * (bz + oz - b.z));
+                            idx = min(max(idx, 0), kTileBox - 1);
+                            const unsigned wd = V.tile_bits[(size_t)t * 32 + (idx >> 5)];
+                            int k = V.tile_wpre[(size_t)t * 32 + (idx >> 5)] + __popc(wd & ((1u << (idx & 31)) - 1u));
+                            k = min(k, kTileCells - 1);
+                            delta = (V.tile_off[(size_t)t * kTileCells + k] - s_cell[w][lane].x) * 64;
+                        }
+                        s_delta[w][X][code] = delta;
+                    }
+                }
                 __syncwarp();
                 // this lane as a home atom: its list
                 const int p = hbase + lane;
+                const int tsel = (tpa_atoms && p / tpa_atoms != tA) ? 1 : 0;
                 size_t slot = (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
                 const int jump = (32 << lq) - (tq - 1);
                 int mycnt = 0;
@@ -409,7 +585,8 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                     while (t == 0u && ++r < rb) t = s_t[w][r][lane];
                     while (__any_sync(0xffffffffu, r < rb)) {
                         if (r < rb) {
-                            const uint32_t ec = s_e[w][r][__ffs(t) - 1];
+                            uint32_t ec = s_e[w][r][__ffs(t) - 1];
+                            ec += (uint32_t)s_delta[w][tsel][ec & 63u];
                             if (tq >= 4) {
                                 s_st[w][mycnt & 3][lane] = ec;
                                 if ((mycnt & 3) == 3 && mycnt < maxn)
@@ -610,6 +787,8 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_gather<MD_PREC_FP64>
                                                : (const void *)k_gather<MD_PREC_MIXED>,
                         dim3(nb), dim3(256), 0, a});
+    if (V.tile_atoms > 0)
+        seq.push_back(KCall{(const void *)k_tiles, dim3((V.n_ftiles + 3) / 4), dim3(128), 0, a});
     const void *kb;
     if (V.prec == MD_PREC_FP64)
         kb = V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>;

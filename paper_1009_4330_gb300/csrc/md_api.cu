@@ -41,7 +41,8 @@ struct md_system {
     std::vector<void *> allocs;
     PairTab *d_tab = nullptr;
     Ctl *d_ctl = nullptr;
-    int block = 256;
+    int block = 128;
+    int staging = 0;  // block-local lists with shared-memory staging (md_set_staging)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t gp_part_size = 0;
@@ -252,6 +253,31 @@ static md_status settle_overflow(md_system *h, bool all) {
         if (st) return st;
     }
     return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list still overflowing after growing");
+}
+
+// Block-local lists (opt-in, md_set_staging) for the mixed-precision full-list force passes: a force
+// block of `block` threads covers tile_atoms = block / T atoms and stages the
+// records of the cells around them.  Used when the tile is 32..128 atoms and
+// the staged set of an average tile fits comfortably in kTileCap records
+// (estimate: a cube of tile_atoms / atoms-per-cell cells, dilated by one cell,
+// 30 % above that for the shapes of Morton-ordered cell runs); tiles that do
+// not fit fall back to slot entries one by one.  Returns 1 if tile_atoms changed.
+static int set_tiles(md_system *h) {
+    View &V = h->V;
+    const int old = V.tile_atoms;
+    int ta = 0;
+    if (h->staging && V.prec == MD_PREC_MIXED && !V.half && h->block % V.tpa == 0) {
+        ta = h->block / V.tpa;
+        double apc = 0.0;  // atoms per cell, densest replica
+        for (const Rep &R : h->reps) apc = std::max(apc, (double)R.natoms / (double)R.nbins);
+        const double side = std::cbrt(ta / std::max(apc, 1e-9) + 1.0) + 2.0;
+        const double est = 1.3 * side * side * side * apc;
+        if (ta < 32 || ta > 128 || est > kTileCap) ta = 0;
+    }
+    V.tile_atoms = ta;
+    V.n_ftiles = ta ? (V.n_pad + ta - 1) / ta : 0;
+    if (ta != old) drop_graph(h);
+    return ta != old;
 }
 
 static md_status full_rebuild(md_system *h, bool staged) {
@@ -497,6 +523,17 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.scan_blk, (size_t)(V.nbins_total + 4095) / 4096 + 1);
     AL(V.rep_base, (size_t)n_rep);
     AL(V.ncount, n);
+    {
+        // tile tables sized for the smallest tile (32 atoms)
+        const size_t nt = (n + 31) / 32;
+        AL(V.tile_cnt, nt);
+        AL(V.tile_ncell, nt);
+        AL(V.tile_first, nt * kTileCells);
+        AL(V.tile_off, nt * kTileCells);
+        AL(V.tile_box, nt);
+        AL(V.tile_bits, nt * 32);
+        AL(V.tile_wpre, nt * 32);
+    }
     if (V.pot == MD_POT_EAM_FS) {
         if (V.prec == MD_PREC_FP64) AL(V.fp64, n);
         else AL(V.fp32, n);
@@ -582,6 +619,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
 #undef CKD
     md_status st = upload_tab(h);
     if (st) { md_destroy(h); return st; }
+    set_tiles(h);
     st = full_rebuild(h, true);
     if (st) { md_destroy(h); return st; }
     st = compute_forces(h, kModeStoreF);
@@ -662,6 +700,7 @@ md_status md_step(md_system *h, int64_t nsteps) {
         if (st) return st;
         if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity in md_step");
         if (c.err & kErrTimeout) return fail(h, MD_ERR_TIMEOUT, "device wait timed out");
+        if (c.err & kErrConfig) return fail(h, MD_ERR_INVALID, "force launch does not match the list's tiles");
         if (!(c.err & kErrOverflow)) {
             if (c.remaining != 0) return fail(h, MD_ERR_CUDA, "step loop ended with %d steps left", c.remaining);
             return MD_OK;
@@ -697,6 +736,7 @@ md_status md_step_eager(md_system *h, int64_t nsteps) {
     md_status st = read_ctl(h, &c);
     if (st) return st;
     if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity in md_step_eager");
+    if (c.err & kErrConfig) return fail(h, MD_ERR_INVALID, "force launch does not match the list's tiles");
     if (c.err & kErrOverflow) return fail(h, MD_ERR_LIST_OVERFLOW, "list overflow in md_step_eager (use md_step)");
     return MD_OK;
 }
@@ -782,7 +822,7 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
     if (block != 64 && block != 128 && block != 256) return fail(h, MD_ERR_INVALID, "block must be 64, 128 or 256");
     if (vec != 1 && vec != 2 && vec != 4) return fail(h, MD_ERR_INVALID, "vec must be 1, 2 or 4");
     const int half = list == MD_LIST_HALF ? 1 : 0;
-    const bool relayout = (tpa != h->V.tpa) || (half != h->V.half) || (vec != h->V.vec);
+    bool relayout = (tpa != h->V.tpa) || (half != h->V.half) || (vec != h->V.vec);
     h->V.tpa = tpa;
     h->V.half = half;
     h->V.vec = vec;
@@ -790,7 +830,16 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
     h->V.lvec = ilog2(vec);
     h->block = block;
     drop_graph(h);
+    if (set_tiles(h)) relayout = true;
     if (relayout) return md_build_neighbors(h);
+    return MD_OK;
+}
+
+md_status md_set_staging(md_system *h, int32_t on) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    h->staging = on ? 1 : 0;
+    drop_graph(h);
+    if (set_tiles(h)) return md_build_neighbors(h);
     return MD_OK;
 }
 
@@ -941,6 +990,15 @@ md_status md_info(md_system *h, md_info_t *out) {
     out->rebuilds = c.rebuilds;
     out->steps = c.steps;
     for (int a = 0; a < 3; ++a) out->bins[a] = h->reps[0].nb[a];
+    out->tile_atoms = h->V.tile_atoms;
+    out->n_tiles_force = h->V.n_ftiles;
+    out->tiles_staged = 0;
+    if (h->V.n_ftiles > 0) {
+        std::vector<int> tc(h->V.n_ftiles);
+        CK(h, cudaMemcpyAsync(tc.data(), h->V.tile_cnt, sizeof(int) * tc.size(), cudaMemcpyDeviceToHost, h->s));
+        CK(h, cudaStreamSynchronize(h->s));
+        for (int c : tc) out->tiles_staged += (c >= 0) ? 1 : 0;
+    }
     return MD_OK;
 }
 
@@ -968,6 +1026,7 @@ md_status md_sync_status(md_system *h) {
         CK(h, cudaStreamSynchronize(h->s));
         if (c.err & kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite state detected on the device");
         if (c.err & kErrTimeout) return fail(h, MD_ERR_TIMEOUT, "device wait timed out");
+        if (c.err & kErrConfig) return fail(h, MD_ERR_INVALID, "force launch does not match the list's tiles");
         if (c.err & kErrOverflow) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list overflow");
     }
     return MD_OK;

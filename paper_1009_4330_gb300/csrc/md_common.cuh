@@ -41,7 +41,15 @@ constexpr uint32_t kSelfCode = 0x15u;  // dx = dy = dz = 0
 constexpr int kMaxBinsPerAxis = 1023;
 
 // status bits latched in Ctl::err (first error code is also kept in Ctl::code)
-enum : unsigned { kErrOverflow = 1u, kErrNonfinite = 2u, kErrTimeout = 4u };
+enum : unsigned { kErrOverflow = 1u, kErrNonfinite = 2u, kErrTimeout = 4u, kErrConfig = 8u };
+
+// Block-local lists: force block b owns the tile of tile_atoms consecutive
+// slots [b tile_atoms, (b+1) tile_atoms), stages the records of every cell
+// within one cell of its atoms' cells in shared memory, and its atoms' list
+// entries hold offsets into that staging instead of slots.
+constexpr int kTileCap = 2048;    // staged records per tile (power of two)
+constexpr int kTileCells = 128;   // cells staged per tile
+constexpr int kTileBox = 1024;    // cells in the tile's dilated bounding box (bitmap of 32 words)
 
 struct Rep {                // one replica (periodic box), device-resident
     double L[3];            // box edges
@@ -131,6 +139,15 @@ struct View {
     double *gs, *gx;      // [3][n_pad] gradient in / out (sorted)
     double *bw;           // [2][n_pad] EAM backward: F'(rho_i), mu_i = lambda_i F''(rho_i)
     double *gp_part;      // per block partial parameter gradients
+    // block-local lists (tile_atoms = 0: every list entry holds a slot)
+    int tile_atoms, n_ftiles;
+    int *tile_cnt;        // [n_ftiles] staged records; -1: this tile's entries hold slots
+    int *tile_ncell;      // [n_ftiles]
+    int *tile_first;      // [n_ftiles][kTileCells] slot of the first record of each staged cell, in box order
+    int *tile_off;        // [n_ftiles][kTileCells] its first staged record
+    int4 *tile_box;       // [n_ftiles] box corner (unwrapped cell coordinates), dims x | y << 16
+    unsigned *tile_bits;  // [n_ftiles][32] cells of the tile's union within the box
+    int *tile_wpre;       // [n_ftiles][32] popcount prefix of tile_bits
     const PairTab *tab;
     Ctl *ctl;
     cudaGraphConditionalHandle cond_loop, cond_rebuild;
@@ -258,6 +275,84 @@ struct KahanF {
 };
 
 __device__ __forceinline__ void latch_error(Ctl *ctl, unsigned bit) { atomicOr(&ctl->err, bit); }
+
+// slot of the neighbour that entry e of atom p's list names: the entry itself,
+// or for a block-local list the staged record's cell start plus its rank there
+__device__ __forceinline__ int entry_slot(const View &V, int p, uint32_t e) {
+    const int jl = (int)(e >> 6);
+    if (V.tile_atoms == 0) return jl;
+    const int t = p / V.tile_atoms;
+    if (V.tile_cnt[t] < 0) return jl;
+    const int *off = V.tile_off + (size_t)t * kTileCells;
+    int lo = 0, hi = V.tile_ncell[t] - 1;  // last cell whose first record is <= jl
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= jl) lo = mid;
+        else hi = mid - 1;
+    }
+    return V.tile_first[(size_t)t * kTileCells + lo] + (jl - off[lo]);
+}
+
+// Dynamic shared memory of a force block with block-local lists: the staged
+// records, then the tile's cell table (first slot, first staged record).
+constexpr size_t kTileSmem = (size_t)kTileCap * 16 + 2 * (kTileCells + 1) * sizeof(int);
+
+// largest k < nc with off[k] <= l (off ascending, off[0] = 0)
+__device__ __forceinline__ int tile_cell_of(const int *off, int nc, int l) {
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= l) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// copy the records of tile t's cells into s_rec, all threads of the block:
+// the cell table first, then every thread copies records l, l + blockDim, ...
+// four at a time (independent loads in flight).  Ends with a block barrier.
+__device__ __forceinline__ void stage_tile(const View &V, int t, float4 *s_rec) {
+    int *s_first = (int *)(s_rec + kTileCap);
+    int *s_off = s_first + kTileCells + 1;
+    const int nc = V.tile_ncell[t], tot = min(V.tile_cnt[t], kTileCap);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        s_first[k] = V.tile_first[(size_t)t * kTileCells + k];
+        s_off[k] = V.tile_off[(size_t)t * kTileCells + k];
+    }
+    __syncthreads();
+    const int bd = blockDim.x;
+    for (int l0 = threadIdx.x; l0 < tot; l0 += 4 * bd) {
+        int src[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int l = l0 + u * bd;
+            src[u] = -1;
+            if (l < tot) {
+                const int k = tile_cell_of(s_off, nc, l);
+                src[u] = s_first[k] + (l - s_off[k]);
+            }
+        }
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (src[u] >= 0) v[u] = V.rec[src[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (src[u] >= 0) s_rec[l0 + u * bd] = v[u];
+    }
+}
+
+// tile mode of this block: 1 = its atoms' entries are block-local (stage the
+// records), 0 = they hold slots, -1 = the launch does not cover exactly one
+// tile per block (error latched; the block must not walk its lists)
+__device__ __forceinline__ int tile_mode(const View &V, int T) {
+    if (V.tile_atoms == 0) return 0;
+    if ((int)blockDim.x != V.tile_atoms * T || (int)blockIdx.x >= V.n_ftiles) {
+        if (threadIdx.x == 0) latch_error(V.ctl, kErrConfig);
+        return -1;
+    }
+    return V.tile_cnt[blockIdx.x] >= 0 ? 1 : 0;
+}
 
 // last-block-done ticket: returns true in every thread of the last block to
 // arrive (all earlier blocks' global writes are visible to it), false in all

@@ -241,7 +241,7 @@ class System:
     def autotune(self, cache_path=None):
         self._call("md_autotune", cache_path.encode() if cache_path else None)
 
-    def set_kernel(self, tpa, list="full", block=256, vec=None):
+    def set_kernel(self, tpa, list="full", block=128, vec=None):
         """Force-kernel variant; vec (list entries per thread per load) defaults to 4 for tpa <= 8, else 1."""
         if vec is None:
             vec = 4 if tpa <= 8 else 1
@@ -249,6 +249,10 @@ class System:
 
     def sync_status(self):
         self._call("md_sync_status")
+
+    def set_staging(self, on=True):
+        """Block-local lists with shared-memory staging of each force block's cells (off by default)."""
+        self._call("md_set_staging", ctypes.c_int32(1 if on else 0))
 
     def time_gather(self, warmup=3, reps=20):
         """ms per pass of the force kernel's memory-only twin (mixed LJ, full list)"""

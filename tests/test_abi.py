@@ -42,7 +42,7 @@ def test_struct_layout_matches_header():
     # md_config: 16 fields, pointer-aligned; the ctypes mirror must have the C size
     from paper_1009_4330_gb300 import _lib
     assert ctypes.sizeof(_lib.MdConfig) == 128
-    assert ctypes.sizeof(_lib.MdInfo) == 80
+    assert ctypes.sizeof(_lib.MdInfo) == 88
 
 
 def test_null_arguments_are_rejected_without_device_work(lib):
@@ -93,3 +93,27 @@ def test_product_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_ctypes_mirrors_match_the_c_header(tmp_path):
+    # compile a probe against include/md.h and compare sizes and field offsets
+    import shutil
+    import subprocess
+    from paper_1009_4330_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    fields = [f for f, _ in _lib.MdInfo._fields_]
+    src = tmp_path / "probe.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"md.h\"\nint main(void) {\n"
+                   "  printf(\"%zu %zu\\n\", sizeof(md_config), sizeof(md_info_t));\n"
+                   + "".join(f"  printf(\"%zu\\n\", offsetof(md_info_t, {f}));\n" for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split()
+    assert int(out[0]) == ctypes.sizeof(_lib.MdConfig)
+    assert int(out[1]) == ctypes.sizeof(_lib.MdInfo)
+    for f, off in zip(fields, out[2:]):
+        assert int(off) == getattr(_lib.MdInfo, f).offset, f
