@@ -372,6 +372,9 @@ def side_runs(synth, cells, K, W):
         inf = s.info()
         alt["staged" if staged else "gathered"] = {"force_ms": fms, "twin_ms": gms, "tiles_staged": inf["tiles_staged"],
                                                    "n_tiles": inf["n_tiles_force"], "block": inf["block"]}
+    # the cell-list force pass (no Verlet list) on the same staged tiles
+    _, cms = s.cell_forces(reps=10)
+    alt["cell_list"] = {"force_ms": cms, "note": "27 cells tested per atom, no list read or built"}
     out["staging_alternative_rc2.5"] = alt
     s.close()
     # rc 5.0, mixed

@@ -212,6 +212,20 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
 md_status md_set_staging(md_system *h, int32_t on);
 
 /*
+ * Cell-list force pass, the alternative to neighbour lists that the paper
+ * measures (Sec. III.C): each atom tests every atom of the 27 cells around
+ * its cell (cells as binned at the last rebuild, at least rc + skin wide;
+ * atoms have moved less than skin/2 since), with each force block's cells
+ * staged in shared memory -- no Verlet list is read.  Needs mixed-precision
+ * LJ with md_set_staging(1), one thread per atom and 128-thread blocks
+ * (MD_ERR_UNSUPPORTED otherwise).  reps > 0: times `reps` passes as md_step
+ * runs a force pass (velocities read and written, zero kick; after 2 untimed
+ * passes), ms_out (host) = ms per pass.  f_out (device [n][3], original
+ * order, may be NULL): the forces from one pass.  The state is unchanged.
+ */
+md_status md_cell_forces(md_system *h, double *f_out, int32_t reps, double *ms_out);
+
+/*
  * md_step without CUDA graphs: the step's kernels are launched one by one
  * and the list-rebuild kernels every step (each returns at once for replicas
  * whose displacement check did not ask for a rebuild).  Same results as

@@ -19,7 +19,8 @@ MD_MAX_TYPES = 8
 EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "md_compute_forces", "md_step",
            "md_energy_virial", "md_get_state", "md_set_state", "md_set_params", "md_forces_backward",
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
-           "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather", "md_set_staging")
+           "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather", "md_set_staging",
+           "md_cell_forces")
 
 
 class MdConfig(ctypes.Structure):

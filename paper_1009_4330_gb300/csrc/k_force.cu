@@ -360,6 +360,103 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
     if (!HALF) finish_step(V, a);
 }
 
+// Cell-list force pass, no Verlet list (the alternative the paper measures
+// against neighbour lists, Sec. III.C): block b stages tile b's cells as the
+// block-local lists do, and each atom tests every record of the 27 cells
+// around its cell as binned at the last rebuild.  Atoms have moved less than
+// skin/2 since then and cells are at least rc + skin wide, so every pair
+// within rc is among them.  Lanes of one home cell read the same records in
+// the same order (shared-memory broadcasts).  Mixed precision, one thread
+// per atom, one 128-atom tile per block; a tile too dense to stage reads the
+// cells' records from global memory.  Forces only (no energy/virial).
+template <int MT>
+__global__ void __launch_bounds__(128) k_lj_cells(View V, KArgs a) {
+    using P = Pol<MD_PREC_MIXED>;
+    __shared__ float s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
+    __shared__ double s_ftm[kMaxTypes];
+    const int np = V.ntypes * V.ntypes;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) { s_lj1[k] = V.tab->lj1f[k]; s_lj2[k] = V.tab->lj2f[k]; }
+    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    extern __shared__ float4 s_rec[];
+    const int tmode = begin_tile<MD_PREC_MIXED>(V, 1, s_rec);
+    __syncthreads();
+    const unsigned err = V.ctl->err;
+    const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x;
+    LJPair<MD_PREC_MIXED, MT, 0, 0> pr;
+    pr.V = &V;
+    pr.lj1 = s_lj1; pr.lj2 = s_lj2;
+    pr.rc2 = V.rc2f;
+    pr.nt = V.ntypes;
+    pr.n = V.n_pad;
+    pr.ti = 0;
+    pr.ax.zero(); pr.ay.zero(); pr.az.zero();
+    bool valid = false;
+    if (p < V.n_pad && err == 0 && tmode >= 0) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        valid = (p - R.atom0) < R.natoms;
+        if (valid) {
+            float xi, yi, zi;
+            P::load(V, p, xi, yi, zi, pr.ti);
+            const int bk = V.bpk[p];
+            const int bx = unpack_bx(bk), by = unpack_by(bk), bz = unpack_bz(bk);
+            const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
+            const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
+            const int4 box = V.tile_box[t];
+            const int bdx = box.w & 0xffff, bdy = box.w >> 16;
+            const int ncell = V.tile_ncell[t], tot = V.tile_cnt[t];
+            for (int k = 0; k < 27; ++k) {
+                const int row = k / 3;
+                const int ox = k - 3 * row - 1, oy = row % 3 - 1, oz = row / 3 - 1;
+                // this stencil cell's records: staged (offset, count) or global (first slot, count)
+                int first, cnt, base;
+                if (tmode == 1) {
+                    int idx = (bx + ox - box.x) + bdx * ((by + oy - box.y) + bdy * (bz + oz - box.z));
+                    idx = min(max(idx, 0), kTileBox - 1);
+                    const unsigned wd = V.tile_bits[(size_t)t * 32 + (idx >> 5)];
+                    int kc = V.tile_wpre[(size_t)t * 32 + (idx >> 5)] + __popc(wd & ((1u << (idx & 31)) - 1u));
+                    kc = min(kc, ncell - 1);
+                    first = V.tile_off[(size_t)t * kTileCells + kc];
+                    const int nxt = kc + 1 < ncell ? V.tile_off[(size_t)t * kTileCells + kc + 1] : tot;
+                    cnt = min(nxt, kTileCap) - first;
+                    base = V.tile_first[(size_t)t * kTileCells + kc];
+                } else {
+                    int cx = bx + ox, cy = by + oy, cz = bz + oz;
+                    cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
+                    cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
+                    cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
+                    const int gb = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
+                    first = V.bin_start[gb];
+                    cnt = V.bin_count[gb];
+                    base = first;
+                }
+                const float sx = ox * hx, sy = oy * hy, sz = oz * hz;
+                const int self = (k == 13) ? p - base : -1;  // the atom itself, centre image
+                for (int l0 = 0; l0 < cnt; l0 += 4) {
+                    pr.round_begin();
+                    for (int l = l0; l < l0 + 4 && l < cnt; ++l) {
+                        const float4 r4 = (tmode == 1) ? s_rec[(first + l) & (kTileCap - 1)] : V.rec[first + l];
+                        if (l == self) continue;
+                        const float dx = xi - r4.x - sx, dy = yi - r4.y - sy, dz = zi - r4.z - sz;
+                        pr(0u, dx, dy, dz, dx * dx + dy * dy + dz * dz, __float_as_int(r4.w));
+                    }
+                    pr.round_end();
+                }
+            }
+        }
+    }
+    if (valid) epilogue(V, a.mode, rem, p, pr.ti, pr.ax.value(), pr.ay.value(), pr.az.value(), s_ftm);
+    finish_step(V, a);
+}
+
+void cells_force_sequence(const View &V, int mode, std::vector<KCall> &seq) {
+    KArgs a{};
+    a.mode = mode;
+    const void *fn = V.ntypes > 1 ? (const void *)k_lj_cells<1> : (const void *)k_lj_cells<0>;
+    seq.push_back(KCall{fn, dim3((unsigned)V.n_ftiles), dim3(128), kTileSmem, a});
+}
+
 // Memory-only twin of the mixed full-list force pass, for measuring the
 // ceiling of its access pattern: the same list walk and record gathers, the
 // same velocity read/write (with a zero increment), but three additions per

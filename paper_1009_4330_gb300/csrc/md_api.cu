@@ -969,6 +969,37 @@ md_status md_time_gather(md_system *h, int32_t warmup, int32_t reps, double *ms_
     return MD_OK;
 }
 
+md_status md_cell_forces(md_system *h, double *f_out, int32_t reps, double *ms_out) {
+    if (!h || reps < 0 || (reps > 0 && !ms_out)) return fail(h, MD_ERR_INVALID, "bad argument");
+    if (h->cfg.pot != MD_POT_LJ || h->V.prec != MD_PREC_MIXED || h->V.tile_atoms != 128 || h->V.tpa != 1)
+        return fail(h, MD_ERR_UNSUPPORTED,
+                    "md_cell_forces: mixed-precision LJ with md_set_staging(1), one thread per atom, 128-thread blocks");
+    if (reps > 0) {
+        std::vector<KCall> seq;
+        cells_force_sequence(h->V, kModeKickDry, seq);
+        for (int w = 0; w < 2; ++w) CK(h, run_seq(h, seq));
+        cudaEvent_t e0, e1;
+        CK(h, cudaEventCreate(&e0));
+        CK(h, cudaEventCreate(&e1));
+        CK(h, cudaEventRecord(e0, h->s));
+        for (int r = 0; r < reps; ++r) CK(h, run_seq(h, seq));
+        CK(h, cudaEventRecord(e1, h->s));
+        CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *ms_out = (double)ms / reps;
+    }
+    if (f_out) {
+        std::vector<KCall> seq;
+        cells_force_sequence(h->V, kModeStoreF, seq);
+        CK(h, run_seq(h, seq));
+        CK(h, launch_state_out(h->V, nullptr, nullptr, f_out, h->s));
+    }
+    return MD_OK;
+}
+
 md_status md_info(md_system *h, md_info_t *out) {
     if (!h || !out) return fail(h, MD_ERR_INVALID, "null argument");
     Ctl c;

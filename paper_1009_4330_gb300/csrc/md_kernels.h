@@ -32,6 +32,8 @@ void force_sequence(const View &V, int mode, int block, bool in_graph, std::vect
 
 // memory-only twin of the mixed full-list LJ force pass (see md_time_gather)
 void gather_probe_sequence(const View &V, int block, std::vector<KCall> &seq);
+// cell-list LJ force pass (no Verlet list) over the tiles of the last build
+void cells_force_sequence(const View &V, int mode, std::vector<KCall> &seq);
 
 // loop-control kernel placed before the md_step WHILE node
 void loop_init_sequence(const View &V, std::vector<KCall> &seq);

@@ -250,6 +250,13 @@ class System:
     def sync_status(self):
         self._call("md_sync_status")
 
+    def cell_forces(self, reps=0):
+        """Forces (n,3) from the cell-list pass (no Verlet list) and, if reps > 0, its ms per pass."""
+        f = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        ms = ctypes.c_double(0.0)
+        self._call("md_cell_forces", _ptr(f), ctypes.c_int32(int(reps)), ctypes.byref(ms))
+        return f, ms.value
+
     def set_staging(self, on=True):
         """Block-local lists with shared-memory staging of each force block's cells (off by default)."""
         self._call("md_set_staging", ctypes.c_int32(1 if on else 0))

@@ -107,3 +107,43 @@ def test_staged_eam_and_backward_match_oracle(prec):
     assert rel_maxnorm(gx.cpu().numpy(), gx_ref) < 1e-11
     assert np.allclose(gp.cpu().numpy()[1:], gp_ref[1:], rtol=1e-11, atol=1e-11 * np.abs(gp_ref).max())
 
+
+
+@pytest.mark.parametrize("case", ["liquid", "dense_cluster"])
+def test_cell_list_forces_match_oracle(case):
+    # md_cell_forces: no Verlet list, every atom of the 27 cells tested; also
+    # after some steps (atoms moved, cells as binned at the last rebuild)
+    from paper_1009_4330_gb300 import System
+    if case == "liquid":
+        d = lj_case(15, 0.05, seed=1003)
+        x, v, box = d["x"], d["v"], d["box"]
+    else:
+        x, v, box = dense_cluster_case()
+    with System.lj(x, v, box, cutoff=RC, skin=SKIN, dt=0.002, mass=1.0, precision="mixed", tpa=1) as s:
+        s.set_staging(True)
+        assert margin_ok(x, box, RC, margin=RC_MARGIN_MIXED)
+        f_ref = oracle.lj(x, box, RC)[0]
+        f_cell, ms = s.cell_forces(reps=3)
+        assert ms > 0.0
+        assert rel_maxnorm(f_cell.cpu().numpy(), f_ref) < TOL_MIXED
+        if case != "liquid":
+            return  # the density-4 cluster is far from equilibrium: no stepping
+        # after steps, on sampled atoms none of whose pairs lies near rc
+        s.step(7)
+        xs = s.state()[0].cpu().numpy()
+        rng = np.random.default_rng(5)
+        idx = [int(i) for i in rng.choice(xs.shape[0], 96, replace=False)
+               if oracle.min_gap(xs, box, RC, [int(i)]) > RC_MARGIN_MIXED]
+        assert len(idx) > 48
+        fr, _, _ = oracle.lj_at(xs, box, RC, idx)
+        f_cell = s.cell_forces()[0].cpu().numpy()
+        assert rel_maxnorm(f_cell[idx], fr) < TOL_MIXED
+
+
+def test_cell_list_needs_staging():
+    from paper_1009_4330_gb300 import MDError, System
+    d = lj_case(15, 0.02, seed=1002)
+    with System.lj(d["x"], d["v"], d["box"], cutoff=RC, skin=SKIN, dt=0.005, mass=1.0, precision="mixed",
+                   tpa=1) as s:
+        with pytest.raises(MDError):
+            s.cell_forces()
