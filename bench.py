@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--tpa", type=int, default=0, help="threads per atom (0: set-up mini-benchmark picks)")
     ap.add_argument("--list", default="auto", choices=["auto", "full", "half"])
     ap.add_argument("--vec", type=int, default=0, help="list entries per thread per load (0: default for tpa)")
+    ap.add_argument("--block", type=int, default=128, help="force-kernel threads per block when --tpa is given")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
     ap.add_argument("--profile", default=None, choices=["build", "eam_backward"],
@@ -267,11 +268,13 @@ def run_reference(args, ws, rank):
 
 
 # DRAM traffic of the force kernel per atom, from the ncu capture summarised in
-# profiles/k_lj_lj500k_mixed_full.md (dram__bytes_read.sum + dram__bytes_write.sum
-# = 174.3 MB for 500,000 atoms; scaled by atoms, the list length per atom being
-# the same).  Valid for that variant only: T = 1 thread per atom, Q = 4, full list.
-K_LJ_TRAFFIC_PER_ATOM = 174.3e6 / 500000
-K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full"}
+# profiles/k_lj_lj500k_mixed_full.md (the md_step form of the pass:
+# dram__bytes_read.sum + dram__bytes_write.sum = 182.10 + 4.33 MB for 500,000
+# atoms; scaled by atoms, the list length per atom being the same).  Valid for
+# that variant only: T = 1 thread per atom, Q = 4, full list, 128-thread blocks,
+# records gathered (no staging).
+K_LJ_TRAFFIC_PER_ATOM = (182.098176e6 + 4.329472e6) / 500000
+K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full", "block": 128, "tile_atoms": 0}
 
 
 def load_peaks():
@@ -293,7 +296,7 @@ def run_ours(args, ws, rank, local):
     # tpa 0: the set-up mini-benchmark picks threads per atom, list kind and block size
     s, d = make_lj(synth, cells, 2.5, "mixed", tpa=args.tpa, lst=args.list if args.tpa else "auto")
     if args.tpa and args.vec:
-        s.set_kernel(args.tpa, args.list if args.list != "auto" else "full", 256, args.vec)
+        s.set_kernel(args.tpa, args.list if args.list != "auto" else "full", args.block, args.vec)
     n = d["x"].shape[0]
     K, W = args.steps, max(3, args.warmup)
     barrier(dist)
