@@ -363,6 +363,10 @@ def side_runs(synth, cells, K, W):
     n = d["x"].shape[0]
     out["fp64_rc2.5"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"]}
     s.close()
+    # O(N) CPU baseline: velocity Verlet with FP64 cell-list forces on the host
+    # cores, 2 steps of the same 864,000-atom liquid (the cpu_baseline of the
+    # line is the O(N^2) oracle)
+    out["cpu_celllist"] = cpu_celllist(synth, cells)
     # design alternative: block-local lists with shared-memory staging (off by
     # default), force pass and its memory-only twin against the default layout
     s, d = make_lj(synth, cells, 2.5, "mixed", tpa=1, lst="full")
@@ -421,6 +425,18 @@ def side_runs(synth, cells, K, W):
     s.close()
     torch.cuda.synchronize()
     return out
+
+
+def cpu_celllist(synth, cells, steps=2):
+    import oracle
+    d = synth.config1(rc=2.5, cells=cells)
+    f = oracle.lj_cells(d["x"], d["box"], 2.5)
+    t0 = time.perf_counter()
+    oracle.nve_cells(d["x"], d["v"], d["box"], 2.5, d["dt"], 1.0, steps, f=f)
+    dt = time.perf_counter() - t0
+    n = d["x"].shape[0]
+    return {"value": n * steps / dt, "unit": "atom-timesteps/s", "cores": oracle.num_threads(),
+            "kind": "O(N) cell-list FP64 velocity Verlet (host)", "sample": f"{steps} steps of the {n}-atom liquid"}
 
 
 def force_matching_timing(synth, reps=20):

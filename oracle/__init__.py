@@ -73,6 +73,10 @@ def _load():
     lib.oracle_eam.argtypes = [_I64, _d, _d, _d, _d, _d, _d, _d, _d]
     lib.oracle_eam_at.restype = ctypes.c_int
     lib.oracle_eam_vjp.restype = ctypes.c_int
+    lib.oracle_lj_cells.restype = ctypes.c_int
+    lib.oracle_lj_cells.argtypes = [_I64, _d, _d, _D, _d]
+    lib.oracle_nve_cells.restype = ctypes.c_int
+    lib.oracle_nve_cells.argtypes = [_I64, _d, _d, _d, _D, _D, _D, _I64, _d, _I32]
     lib.oracle_eam_vjp.argtypes = [_I64, _d, _d, _d, _d, _d, _d]
     lib.oracle_eam_at.argtypes = [_I64, _d, _d, _d, _I64, _i64, _d, _d]
     lib.oracle_kinetic.restype = _D
@@ -260,6 +264,27 @@ def eam_vjp(x, box, p, g):
     gp = np.zeros(5)
     _check(lib.oracle_eam_vjp(n, _pd(x), _pd(_f64(box)), _pd(_f64(p)), _pd(g), _pd(gx), _pd(gp)), "eam_vjp")
     return gx, gp
+
+
+def lj_cells(x, box, rc):
+    """Single-type LJ forces by cell lists (the O(N) CPU baseline; same sums as lj)."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    f = np.zeros_like(x)
+    _check(lib.oracle_lj_cells(x.shape[0], _pd(x), _pd(_f64(box)), float(rc), _pd(f)), "lj_cells")
+    return f
+
+
+def nve_cells(x, v, box, rc, dt, mass, nsteps, f=None):
+    """Velocity-Verlet with cell-list LJ forces (O(N) CPU baseline): returns (x, v, f)."""
+    lib = _load()
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    have = f is not None
+    f = _f64(f, (-1, 3)).copy() if have else np.zeros_like(x)
+    _check(lib.oracle_nve_cells(x.shape[0], _pd(x), _pd(v), _pd(_f64(box)), float(rc), float(dt), float(mass),
+                                int(nsteps), _pd(f), 1 if have else 0), "nve_cells")
+    return x, v, f
 
 
 def kinetic(v, mass, types=None, ftm2v=1.0) -> float:

@@ -8,7 +8,9 @@
  *
  * Everything here is the plain definition, in FP64, O(N^2) over all pairs
  * with the minimum-image convention in an orthorhombic periodic box whose
- * origin is 0.  Loops over i may run in parallel (OpenMP) because every
+ * origin is 0 -- except the marked O(N) cell-list section, a second route to
+ * the same LJ sums kept as the CPU baseline figure of an O(N) code (pinned
+ * against the definition in the tests).  Loops over i may run in parallel (OpenMP) because every
  * per-atom quantity is written by the one thread that owns atom i; sums over
  * atoms are then taken sequentially in index order, so results do not depend
  * on the thread count.
@@ -531,6 +533,120 @@ int oracle_eam_vjp(int64_t n, const double *x, const double box[3], const double
         for (int q = 0; q < 3; ++q) grad_p[2 + q] = gc[q];
     }
     free(rho); free(fp); free(lam); free(mu); free(gc_i);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* O(N) cell-list CPU baseline (not the oracle's definition)           */
+/* ------------------------------------------------------------------ */
+/*
+ * A plain cell-list evaluation of the same single-type LJ forces, for the
+ * CPU baseline figure that an O(N) CPU code would give (the O(N^2) loops
+ * above are the definition; this is a second route to the same sums, pinned
+ * against them in the tests).  Cells of edge >= rc, at least 3 per axis (so
+ * the 27 neighbour cells are distinct); atoms counting-sorted into cells;
+ * each atom sums over the atoms of its 27 neighbour cells, minimum image per
+ * pair.  Loops over atoms run in parallel; each atom's force is written by
+ * its own thread.  Returns -1 if the box is too small for 3 cells of rc.
+ */
+typedef struct { int nb[3]; double inv[3]; int *start, *order; } cells_t;
+
+static int cells_build(int64_t n, const double *x, const double box[3], double rc, cells_t *c) {
+    for (int a = 0; a < 3; ++a) {
+        c->nb[a] = (int)floor(box[a] / rc);
+        if (c->nb[a] < 3) return -1;
+        c->inv[a] = c->nb[a] / box[a];
+    }
+    const int64_t nc = (int64_t)c->nb[0] * c->nb[1] * c->nb[2];
+    int *cell = (int *)malloc(sizeof(int) * (size_t)n);
+    c->start = (int *)calloc((size_t)nc + 1, sizeof(int));
+    c->order = (int *)malloc(sizeof(int) * (size_t)n);
+    if (!cell || !c->start || !c->order) { free(cell); free(c->start); free(c->order); return -1; }
+    for (int64_t i = 0; i < n; ++i) {
+        int b[3];
+        for (int a = 0; a < 3; ++a) {
+            double w = x[3 * i + a] - box[a] * floor(x[3 * i + a] / box[a]);
+            b[a] = (int)(w * c->inv[a]);
+            if (b[a] >= c->nb[a]) b[a] = c->nb[a] - 1;
+            if (b[a] < 0) b[a] = 0;
+        }
+        cell[i] = (b[2] * c->nb[1] + b[1]) * c->nb[0] + b[0];
+        c->start[cell[i] + 1]++;
+    }
+    for (int64_t k = 0; k < nc; ++k) c->start[k + 1] += c->start[k];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)nc);
+    if (!fill) { free(cell); free(c->start); free(c->order); return -1; }
+    memcpy(fill, c->start, sizeof(int) * (size_t)nc);
+    for (int64_t i = 0; i < n; ++i) c->order[fill[cell[i]]++] = (int)i;
+    free(fill);
+    free(cell);
+    return 0;
+}
+
+static void cells_free(cells_t *c) { free(c->start); free(c->order); }
+
+static void lj_cells_forces(int64_t n, const double *x, const double box[3], double rc, const cells_t *c,
+                            double *f) {
+    const double rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        int b[3];
+        for (int a = 0; a < 3; ++a) {
+            double w = x[3 * i + a] - box[a] * floor(x[3 * i + a] / box[a]);
+            b[a] = (int)(w * c->inv[a]);
+            if (b[a] >= c->nb[a]) b[a] = c->nb[a] - 1;
+            if (b[a] < 0) b[a] = 0;
+        }
+        double fi[3] = {0.0, 0.0, 0.0}, d[3];
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int q[3] = {b[0] + dx, b[1] + dy, b[2] + dz};
+                    for (int a = 0; a < 3; ++a) q[a] = (q[a] + c->nb[a]) % c->nb[a];
+                    const int k = (q[2] * c->nb[1] + q[1]) * c->nb[0] + q[0];
+                    for (int s = c->start[k]; s < c->start[k + 1]; ++s) {
+                        const int j = c->order[s];
+                        if (j == i) continue;
+                        const double r2 = separation(x, i, j, box, d);
+                        if (!(r2 < rc2)) continue;
+                        const double sc = lj_force_over_r(r2, 1.0, 1.0);
+                        for (int a = 0; a < 3; ++a) fi[a] += sc * d[a];
+                    }
+                }
+        for (int a = 0; a < 3; ++a) f[3 * i + a] = fi[a];
+    }
+}
+
+/* single-type LJ (eps = sigma = 1) forces by cell lists */
+int oracle_lj_cells(int64_t n, const double *x, const double box[3], double rc, double *f) {
+    if (n <= 0 || rc <= 0.0) return -1;
+    cells_t c;
+    if (cells_build(n, x, box, rc, &c)) return -1;
+    lj_cells_forces(n, x, box, rc, &c, f);
+    cells_free(&c);
+    return 0;
+}
+
+/* velocity-Verlet NVE (mass m) with cell-list forces, cells rebuilt every step;
+ * f (n*3) holds the forces of x on entry (computed here if `have_f` is 0) and
+ * of the final x on return */
+int oracle_nve_cells(int64_t n, double *x, double *v, const double box[3], double rc, double dt, double m,
+                     int64_t nsteps, double *f, int32_t have_f) {
+    if (n <= 0 || nsteps < 0) return -1;
+    if (!have_f && oracle_lj_cells(n, x, box, rc, f)) return -1;
+    const double hk = 0.5 * dt / m;
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                v[3 * i + a] += hk * f[3 * i + a];
+                x[3 * i + a] += dt * v[3 * i + a];
+            }
+        if (oracle_lj_cells(n, x, box, rc, f)) return -1;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) v[3 * i + a] += hk * f[3 * i + a];
+    }
     return 0;
 }
 
