@@ -446,21 +446,25 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 
 // Verlet list of every atom of a rebuilding replica: all j in the 27 cells
 // around i's cell with |x_i - x_j| < rl.  One warp per home cell (home atoms
-// in chunks of 32).  The 27 neighbour cells form 9 rows of 3 x-adjacent
-// cells; lanes 0..26 fetch the 27 cell bounds at once.  Each row is read as
-// one flat candidate range, 32 candidates at a time, one per lane, shifted
-// into the home cell's frame.  A candidate farther than rl from the bounding
-// box of the home atoms cannot be accepted by any of them (about a quarter of
-// the 27-cell volume); the others go to a per-warp queue in shared memory, in
+// in chunks of 32; a cell with more than 32 atoms is shared out over several
+// warps).  The 27 neighbour cells form 9 rows of 3 x-adjacent cells; lanes
+// 0..26 fetch the 27 cell bounds at once.  Each row is read as one flat
+// candidate range, 32 candidates at a time, one per lane, shifted into the
+// home cell's frame.  A candidate farther than rl from the bounding box of
+// the home atoms cannot be accepted by any of them (about 38 % of the 27-cell
+// candidates); the others go to a per-warp queue in shared memory, in
 // candidate order, and are tested in full rounds of 32.  In a round each lane
 // tests its candidate against every home atom (records broadcast from shared
 // memory) into a 32-bit acceptance mask; a warp bit-matrix transpose turns the
-// candidates' masks into each home atom's mask of accepted candidates, and
-// each home-atom lane appends them to its list in candidate order (warp
-// ballot/prefix compaction in transposed form: deterministic lists, no
-// divergent per-pair bookkeeping).  The test is FP32 with a margin far above
-// its rounding error; pairs inside the margin band are decided in FP64, so
-// the list equals the FP64 definition exactly.  HALF keeps j > i only.
+// candidates' masks into each home atom's mask of accepted candidates.  The
+// masks and entries of up to kBatch rounds are kept in shared memory, and
+// each home-atom lane then appends its accepted candidates in candidate order,
+// moving from round to round through a bitmask of its non-empty rounds (warp
+// ballot/prefix compaction in transposed form: deterministic lists; the loop
+// runs as long as the longest share of the batch, not the sum of each round's
+// longest share).  The test is FP32 with a margin far above its rounding
+// error; pairs inside the margin band are decided in FP64, so the list equals
+// the FP64 definition exactly.  HALF keeps j > i only.
 constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
 constexpr int kBatch = 14;  // rounds whose list entries are appended together
 constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
@@ -471,7 +475,6 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     __shared__ float4 s_q[kBuildWarps][kQueue];  // shifted candidate position, .w = list entry bits
     __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
     __shared__ int2 s_cell[kBuildWarps][27];     // neighbour cells: first slot, count
-    __shared__ uint32_t s_st[kBuildWarps][4][32];  // per home atom: its open group of 4 entries
     __shared__ int s_delta[kBuildWarps][2][64];     // per tile of the chunk, per stencil code: entry shift
     __shared__ uint32_t s_t[kBuildWarps][kBatch][32];  // per round: home atom's mask of accepted candidates
     __shared__ uint32_t s_e[kBuildWarps][kBatch][32];  // per round: candidate's list entry
@@ -577,32 +580,30 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                 // round by round in candidate order: each home-atom lane walks its
                 // own masks, so the loop runs as long as the longest share of the
                 // batch rather than the sum of each round's longest share
-                int rb = 0;  // rounds in the pending batch (warp-uniform)
+                int rb = 0;      // rounds in the pending batch (warp-uniform)
+                unsigned nz = 0u;  // this home atom: rounds of the batch in which it accepts a candidate
                 auto append = [&]() {
                     __syncwarp();
-                    int r = 0;
-                    unsigned t = s_t[w][0][lane];
-                    while (t == 0u && ++r < rb) t = s_t[w][r][lane];
+                    int r = nz ? __ffs(nz) - 1 : rb;
+                    unsigned t = r < rb ? s_t[w][r][lane] : 0u;
                     while (__any_sync(0xffffffffu, r < rb)) {
                         if (r < rb) {
                             uint32_t ec = s_e[w][r][__ffs(t) - 1];
-                            ec += (uint32_t)s_delta[w][tsel][ec & 63u];
-                            if (tq >= 4) {
-                                s_st[w][mycnt & 3][lane] = ec;
-                                if ((mycnt & 3) == 3 && mycnt < maxn)
-                                    *(uint4 *)(V.nlist + slot - 3) =
-                                        make_uint4(s_st[w][0][lane], s_st[w][1][lane], s_st[w][2][lane], ec);
-                            } else if (mycnt < maxn) {
-                                V.nlist[slot] = ec;
-                            }
+                            if (tpa_atoms) ec += (uint32_t)s_delta[w][tsel][ec & 63u];
+                            if (mycnt < maxn) V.nlist[slot] = ec;
                             ++mycnt;
                             slot += (mycnt & (tq - 1)) ? 1 : jump;
                             t &= t - 1u;
-                            while (t == 0u && ++r < rb) t = s_t[w][r][lane];
+                            if (t == 0u) {  // next round with an accepted candidate
+                                const unsigned rest = nz & ~((2u << r) - 1u);
+                                r = rest ? __ffs(rest) - 1 : rb;
+                                if (r < rb) t = s_t[w][r][lane];
+                            }
                         }
                     }
                     __syncwarp();
                     rb = 0;
+                    nz = 0u;
                 };
                 // one round: queue entries 0..cnt-1 (cnt <= 32), one per lane
                 auto round = [&](int cnt) {
@@ -654,8 +655,10 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                     if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
                     // lane = home atom: bit c set if candidate lane c is accepted;
                     // kept with the round's entries until the batch is appended
-                    s_t[w][rb][lane] = warp_transpose32(acc, lane);
+                    const unsigned tr = warp_transpose32(acc, lane);
+                    s_t[w][rb][lane] = tr;
                     s_e[w][rb][lane] = e;
+                    nz |= (tr != 0u ? 1u : 0u) << rb;
                     if (++rb == kBatch) append();
                 };
                 // fill the queue from the rows in order until it holds a full
@@ -714,10 +717,6 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                     __syncwarp();
                 }
                 if (rb > 0) append();
-                if (tq >= 4 && lane < nh && (mycnt & 3) && mycnt <= maxn) {
-                    const size_t g = slot - (mycnt & 3);
-                    for (int q = 0; q < (mycnt & 3); ++q) V.nlist[g + q] = s_st[w][q][lane];
-                }
                 if (lane < nh) {
                     V.ncount[p] = min(mycnt, maxn);
                     if (mycnt > maxn) {
