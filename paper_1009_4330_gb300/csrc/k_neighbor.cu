@@ -572,7 +572,8 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                 // this lane as a home atom: its list
                 const int p = hbase + lane;
                 const int tsel = (tpa_atoms && p / tpa_atoms != tA) ? 1 : 0;
-                size_t slot = (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
+                uint32_t *const lbase = V.nlist + (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
+                unsigned slot = 0u;  // offset from lbase
                 const int jump = (32 << lq) - (tq - 1);
                 int mycnt = 0;
                 int qn = 0;  // queued candidates (warp-uniform)
@@ -588,12 +589,28 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
                     unsigned t = r < rb ? s_t[w][r][lane] : 0u;
                     while (__any_sync(0xffffffffu, r < rb)) {
                         if (r < rb) {
-                            uint32_t ec = s_e[w][r][__ffs(t) - 1];
-                            if (tpa_atoms) ec += (uint32_t)s_delta[w][tsel][ec & 63u];
-                            if (mycnt < maxn) V.nlist[slot] = ec;
+                            const uint32_t *row = &s_e[w][r][0];
+                            const int c1 = __ffs(t) - 1;
+                            t &= t - 1u;
+                            uint32_t e1 = row[c1];
+                            const bool two = t != 0u;  // a second entry from the same round
+                            uint32_t e2 = 0u;
+                            if (two) {
+                                e2 = row[__ffs(t) - 1];
+                                t &= t - 1u;
+                            }
+                            if (tpa_atoms) {
+                                e1 += (uint32_t)s_delta[w][tsel][e1 & 63u];
+                                e2 += (uint32_t)s_delta[w][tsel][e2 & 63u];
+                            }
+                            if (mycnt < maxn) lbase[slot] = e1;
                             ++mycnt;
                             slot += (mycnt & (tq - 1)) ? 1 : jump;
-                            t &= t - 1u;
+                            if (two) {
+                                if (mycnt < maxn) lbase[slot] = e2;
+                                ++mycnt;
+                                slot += (mycnt & (tq - 1)) ? 1 : jump;
+                            }
                             if (t == 0u) {  // next round with an accepted candidate
                                 const unsigned rest = nz & ~((2u << r) - 1u);
                                 r = rest ? __ffs(rest) - 1 : rb;
