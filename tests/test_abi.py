@@ -117,3 +117,32 @@ def test_ctypes_mirrors_match_the_c_header(tmp_path):
     assert int(out[1]) == ctypes.sizeof(_lib.MdInfo)
     for f, off in zip(fields, out[2:]):
         assert int(off) == getattr(_lib.MdInfo, f).offset, f
+
+
+def test_empty_and_oversized_systems_rejected_on_host(lib):
+    # no atoms, and more atoms than the 26-bit list entries can name: refused
+    # before any device allocation
+    from paper_1009_4330_gb300 import _lib
+    import numpy as np
+    p = np.array([1.0, 1.0])
+    m = np.array([1.0])
+    cfg = _lib.MdConfig()
+    cfg.n_types = 1
+    for k in range(3):
+        cfg.box[k] = 1000.0
+    cfg.pot = _lib.MD_POT_LJ
+    cfg.params = p.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.n_params = 2
+    cfg.cutoff, cfg.skin, cfg.dt = 2.5, 0.3, 0.005
+    cfg.mass = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.ftm2v = 1.0
+    cfg.prec = _lib.MD_PREC_MIXED
+    cfg.list = _lib.MD_LIST_FULL
+    cfg.tpa = 1
+    dummy = ctypes.c_void_p(16)  # never dereferenced
+    h = ctypes.c_void_p()
+    cfg.n_atoms = 0
+    assert lib.md_create(ctypes.byref(cfg), dummy, dummy, dummy, ctypes.byref(h)) == _lib.MD_ERR_INVALID
+    cfg.n_atoms = (1 << 26) + 1
+    assert lib.md_create(ctypes.byref(cfg), dummy, dummy, dummy, ctypes.byref(h)) == _lib.MD_ERR_UNSUPPORTED
+    assert not h.value
