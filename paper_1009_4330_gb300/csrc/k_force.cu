@@ -225,10 +225,13 @@ __device__ __forceinline__ void finish_step(const View &V, const KArgs &a) {
     if (last_block(&V.ctl->ticket_force)) {
         if (threadIdx.x == 0) {
             V.ctl->ticket_force = 0;
-            const int rem = V.ctl->remaining - 1;
+            // a latched error made this pass skip its work: the step is not done
+            // (the host finishes it after recovering from a list overflow)
+            const bool done = V.ctl->err == 0;
+            const int rem = V.ctl->remaining - (done ? 1 : 0);
             V.ctl->remaining = rem;
-            if (V.ctl->err == 0) V.ctl->steps += 1;
-            if (a.in_graph) cudaGraphSetConditional(V.cond_loop, (rem > 0 && V.ctl->err == 0) ? 1u : 0u);
+            if (done) V.ctl->steps += 1;
+            if (a.in_graph) cudaGraphSetConditional(V.cond_loop, (rem > 0 && done) ? 1u : 0u);
         }
     }
 }
