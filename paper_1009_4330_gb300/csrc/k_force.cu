@@ -822,11 +822,8 @@ __device__ __forceinline__ float drift_pair(const View &V, int p, int first, int
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
-    __shared__ float s_m[kDriftPer * 8];
-    __shared__ int s_r[kDriftPer * 8];
     const unsigned err = V.ctl->err;
     const int first = V.ctl->first;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float d2[kDriftPer];
     int rep[kDriftPer];
     if constexpr (PREC == MD_PREC_MIXED) {
@@ -855,24 +852,7 @@ __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
         }
     }
 #pragma unroll
-    for (int u = 0; u < kDriftPer; ++u) {
-        const float wm = warp_max(d2[u]);
-        if (lane == 0) { s_m[u * 8 + w] = wm; s_r[u * 8 + w] = rep[u]; }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // merge runs of warps of the same replica, one atomic per run
-        int cr = -1;
-        float cm = 0.f;
-        for (int k = 0; k < kDriftPer * (int)(blockDim.x >> 5); ++k) {
-            if (s_r[k] != cr) {
-                if (cr >= 0 && cm > 0.f) atomicMax(&V.rep_disp[cr], __float_as_uint(cm));
-                cr = s_r[k];
-                cm = 0.f;
-            }
-            cm = fmaxf(cm, s_m[k]);
-        }
-        if (cr >= 0 && cm > 0.f) atomicMax(&V.rep_disp[cr], __float_as_uint(cm));
-    }
+    for (int u = 0; u < kDriftPer; ++u) note_disp(V.rep_disp, V.skin_half2f, d2[u], rep[u]);
     if (last_block(&V.ctl->ticket_drift)) {
         int any = 0;
         bool bad = false;

@@ -253,6 +253,18 @@ __device__ __forceinline__ float warp_max(float x) {
     return x;
 }
 
+// Per-replica maximum squared displacement since the last build, for one warp
+// (inside one replica; rep < 0: none) without a block barrier: only a warp
+// with an atom beyond skin/2 (or non-finite, d2 = +Inf) takes an atomic, so
+// the maximum is exact wherever it decides a rebuild and the steps that need
+// no rebuild take no atomics.
+__device__ __forceinline__ void note_disp(unsigned *rep_disp, float thresh, float d2, int rep) {
+    if (__any_sync(0xffffffffu, d2 > thresh)) {
+        const float wm = warp_max(d2);
+        if ((threadIdx.x & 31) == 0 && rep >= 0) atomicMax(&rep_disp[rep], __float_as_uint(wm));
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
