@@ -222,27 +222,29 @@ __device__ __forceinline__ float code_z16(uint32_t e) {
 }
 
 // FP64 reciprocal by Newton-Raphson (y <- y (2 - x y), quadratic convergence)
-// from the FP32 hardware approximation (relative error < 2^-22): three steps
-// reach double precision.  For 0 < x < FLT_MAX (squared distances here).
+// from the FP32 hardware approximation (relative error < 2^-22, plus 2^-24
+// from rounding x to FP32): one step reaches ~2^-44, and the final step in
+// residual form, y + y (1 - x y) with fused multiply-adds, ~2^-88 before the
+// last rounding, i.e. double precision.  For 0 < x < FLT_MAX (squared
+// distances here).
 __device__ __forceinline__ double rcp_newton(double x) {
     float xf = (float)x, yf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
     double y = (double)yf;
-    y = y * fma(-x, y, 2.0);
     y = y * fma(-x, y, 2.0);
     const double e = fma(-x, y, 1.0);
     return fma(y, e, y);
 }
 
 // FP64 reciprocal square root by Newton-Raphson (y <- y (3 - x y^2) / 2)
-// from the FP32 hardware approximation: three steps reach double precision.
-// For FLT_MIN < x < FLT_MAX.
+// from the FP32 hardware approximation (relative error ~2^-22): the error
+// roughly squares per step (times 3/2), so two steps reach double precision
+// up to the last roundings.  For FLT_MIN < x < FLT_MAX.
 __device__ __forceinline__ double rsqrt_newton(double x) {
     float xf = (float)x, yf;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
     double y = (double)yf;
     const double hx = 0.5 * x;
-    y = y * fma(-hx, y * y, 1.5);
     y = y * fma(-hx, y * y, 1.5);
     y = y * fma(-hx, y * y, 1.5);
     return y;
