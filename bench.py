@@ -147,8 +147,9 @@ class ClockSampler:
 def make_lj(synth, cells, rc, prec, tpa=0, lst="auto"):
     from paper_1009_4330_gb300 import System
     d = synth.config1(rc=rc, cells=cells)
+    # energies reported shifted (continuous at rc, for the drift); forces are the same
     s = System.lj(d["x"], d["v"], d["box"], cutoff=rc, skin=d["skin"], dt=d["dt"], mass=1.0, precision=prec,
-                  list=lst, tpa=tpa)
+                  list=lst, tpa=tpa, energy_shift=True)
     return s, d
 
 
@@ -156,10 +157,12 @@ def info0_is_full(s):
     return s.info()["list"] == "full"
 
 
-def time_steps(s, K, W, sampler_gpu=None, eager=False):
+def time_steps(s, K, W, sampler_gpu=None, eager=False, before=None):
     import torch
     s.step(W, eager=eager)
     torch.cuda.synchronize()
+    if before is not None:
+        before()
     i0 = s.info()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -176,6 +179,29 @@ def time_steps(s, K, W, sampler_gpu=None, eager=False):
     i1 = s.info()
     ms = e0.elapsed_time(e1)
     return ms, i0, i1, (clocks.summary() if clocks else None)
+
+
+def total_energy(s):
+    ev = s.energy_virial()[0].cpu().numpy()
+    return float(ev[0] + ev[1])
+
+
+def accuracy_report(s, d, e_start, K):
+    """Mixed precision against the plain FP64 GPU path (which the tests hold to
+    the FP64 oracle at 1e-12): the force error at the state after the timed
+    steps, and the NVE drift of the shifted total energy over those steps."""
+    from paper_1009_4330_gb300 import System
+    n = d["x"].shape[0]
+    drift = (total_energy(s) - e_start) / n * (1000.0 / K)
+    x, v, _ = s.state()
+    f_mixed = s.compute_forces().cpu().numpy()
+    with System.lj(x, v, d["box"], cutoff=d["rc"], skin=d["skin"], dt=d["dt"], mass=1.0, precision="fp64",
+                   list="full", tpa=4) as s64:
+        f64 = s64.compute_forces().cpu().numpy()
+    err = float(np.abs(f_mixed - f64).max() / np.abs(f64).max())
+    return {"mixed_force_rel_maxnorm_vs_fp64": err, "force_tolerance": 1e-5,
+            "nve_drift_per_atom_per_1000_steps": drift, "drift_bound": 1e-4,
+            "energy": "shifted LJ (continuous at rc)", "state": f"after the {K} timed steps"}
 
 
 def e2e_run(s, d, K):
@@ -300,8 +326,11 @@ def run_ours(args, ws, rank, local):
     n = d["x"].shape[0]
     K, W = args.steps, max(3, args.warmup)
     barrier(dist)
-    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local, eager=args.eager)
+    e_start = []
+    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local, eager=args.eager,
+                                    before=lambda: e_start.append(total_energy(s)))
     ms = max_over_ranks(dist, ms)
+    accuracy = accuracy_report(s, d, e_start[0], K) if rank == 0 else None
     value = ws * n * K / (ms / 1000.0)
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
     # our kernels in the timed region: loop control once, per step the drift and
@@ -343,6 +372,7 @@ def run_ours(args, ws, rank, local):
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "extras": extras,
         }
