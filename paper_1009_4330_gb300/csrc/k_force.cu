@@ -255,6 +255,18 @@ struct LJPair {
     __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
     __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int tj) {
+        // mixed full list, forces only: branch-free (the skin entries' terms are
+        // computed, finite since r2 >= rc^2 there, and zeroed) -- measured faster
+        // than skipping them under a per-lane branch
+        if constexpr (!HALF && !EV && PREC == MD_PREC_MIXED) {
+            const int tp = MT ? ti * nt + tj : 0;
+            const real r2i = Pol<PREC>::rcp(r2);
+            const real r6i = r2i * r2i * r2i;
+            real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
+            fpair = (r2 < rc2) ? fpair : (real)0;
+            rx += dx * fpair; ry += dy * fpair; rz += dz * fpair;
+            return;
+        }
         if (r2 < rc2) {
             const int tp = MT ? ti * nt + tj : 0;
             const real r2i = Pol<PREC>::rcp(r2);
@@ -576,6 +588,12 @@ struct RhoPair {
     __device__ __forceinline__ void round_begin() { part = 0; }
     __device__ __forceinline__ void round_end() { acc.add(part); }
     __device__ __forceinline__ void operator()(uint32_t, real, real, real, real r2, int) {
+        if constexpr (PREC == MD_PREC_MIXED) {  // branch-free: t = 0 beyond rc
+            const real r = r2 * Pol<PREC>::rsqrt(r2);
+            const real t = (r2 < rc2) ? rc - r : (real)0;
+            part += t * t;
+            return;
+        }
         if (r2 < rc2) {
             const real r = r2 * Pol<PREC>::rsqrt(r2);
             const real t = rc - r;
@@ -644,6 +662,17 @@ struct EamPair {
     __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
     __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int wj) {
+        if constexpr (PREC == MD_PREC_MIXED && !EV) {  // branch-free: t = 0 beyond rc zeroes the term
+            const real fpj = (real)__int_as_float(wj);
+            const real rinv = Pol<PREC>::rsqrt(r2);
+            const real r = r2 * rinv;
+            const real t = (r2 < rc2) ? rc - r : (real)0;
+            const real poly = c0 + r * (c1 + r * c2);
+            const real dpoly = c1 + (real)2 * c2 * r;
+            const real coef = -t * ((real)-2 * poly + t * dpoly - (real)2 * (fpi + fpj)) * rinv;
+            rx += dx * coef; ry += dy * coef; rz += dz * coef;
+            return;
+        }
         if (r2 < rc2) {
             // mixed: F'_j came with the record (rec.w, set by the density pass)
             const real fpj = (PREC == MD_PREC_FP64) ? Pol<PREC>::fp(*V, entry_j(ent)) : (real)__int_as_float(wj);
