@@ -107,6 +107,13 @@ __device__ __forceinline__ double group_sum(double x) {
     return x;
 }
 
+// |d|^2 with its operations spelled out (no contraction left to the compiler),
+// so that a pair's FP32 r^2 recomputed after the walk is the walk's own
+template <class real>
+__device__ __forceinline__ real pair_r2(real dx, real dy, real dz) {
+    return fma(dz, dz, fma(dy, dy, dx * dx));
+}
+
 // Walk this thread's share of atom i's list: rounds of T*Q entries, the
 // thread's Q entries arriving in one (vector) load, the next round's load
 // issued before this round's work; the Q records are gathered before any
@@ -155,7 +162,7 @@ __device__ __forceinline__ void walk_list(const View &V, const uint32_t *lp, int
                 const real dx = fma(-(real)code_x(e), hx, xi - xj[q]);
                 const real dy = fma(-(real)code_y4(e), hy4, yi - yj[q]);
                 const real dz = fma(-(real)code_z16(e), hz16, zi - zj[q]);
-                const real r2 = dx * dx + dy * dy + dz * dz;
+                const real r2 = pair_r2(dx, dy, dz);
                 pair(e, dx, dy, dz, r2, tj[q]);
             }
         }
@@ -238,6 +245,20 @@ __device__ __forceinline__ void finish_step(const View &V, const KArgs &a) {
 
 // ---------------------------------------------------------------- LJ ----
 
+// The FP64 path's cut-off decision for the pair (p, entry e) of a mixed pass,
+// from the FP64 positions with the same formula (rare: only pairs whose FP32
+// r^2 lies within rc2f_band of rc^2 -- the unshifted LJ force jumps at rc, so
+// there a decision that differs from FP64 would move F_i by ~|f(rc)|).
+__device__ __forceinline__ bool in_cut_fp64(const View &V, int p, uint32_t e) {
+    const int n = V.n_pad;
+    const int j = entry_slot(V, p, e);
+    const Rep &R = V.rep[V.tile_rep[p >> 5]];
+    const double dx = fma(-(double)entry_dx(e), R.h[0], V.xr[p] - V.xr[j]);
+    const double dy = fma(-(double)entry_dy(e), R.h[1], V.xr[n + p] - V.xr[n + j]);
+    const double dz = fma(-(double)entry_dz(e), R.h[2], V.xr[2 * n + p] - V.xr[2 * n + j]);
+    return dx * dx + dy * dy + dz * dz < V.rc2;
+}
+
 // FULL: every neighbour in i's list, F_i only, no atomics.
 // HALF: each pair once; F_j -= f_ij by FP64 atomics, F_i += sum by one atomic
 //       per component at the end (F zeroed beforehand; kick in k_kick).
@@ -249,9 +270,18 @@ struct LJPair {
     const real *lj1, *lj2, *lj3, *lj4, *off;
     real rc2;
     int ti, nt, n;
+    real near_min;  // mixed: the smallest |r^2 - rc^2| of this thread's pairs
     Acc ax, ay, az, e;
     Acc w[6];
     real rx, ry, rz;  // this round's plain partial sums
+    __device__ __forceinline__ bool in_cut(real r2) {
+        if constexpr (PREC == MD_PREC_MIXED) {
+            const real t = r2 - rc2;  // t < 0 exactly when r2 < rc2
+            near_min = fminf(near_min, fabsf(t));
+            return t < (real)0;
+        }
+        return r2 < rc2;
+    }
     __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
     __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int tj) {
@@ -263,11 +293,11 @@ struct LJPair {
             const real r2i = Pol<PREC>::rcp(r2);
             const real r6i = r2i * r2i * r2i;
             real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
-            fpair = (r2 < rc2) ? fpair : (real)0;
+            fpair = in_cut(r2) ? fpair : (real)0;
             rx += dx * fpair; ry += dy * fpair; rz += dz * fpair;
             return;
         }
-        if (r2 < rc2) {
+        if (in_cut(r2)) {
             const int tp = MT ? ti * nt + tj : 0;
             const real r2i = Pol<PREC>::rcp(r2);
             const real r6i = r2i * r2i * r2i;
@@ -290,15 +320,100 @@ struct LJPair {
     }
 };
 
-// resident blocks of 256 threads asked of the register allocator: fewer live
-// registers for smaller Q leave room for more warps to hide gather latency
-template <int PREC, int Q, int EV>
-struct LjOcc {
-    static constexpr int value = (PREC == MD_PREC_MIXED && !EV) ? (Q == 4 ? 4 : (Q == 2 ? 5 : 6)) : 1;
+// Mixed: every pair near rc gets the FP64 path's cut-off decision.  A
+// thread whose pairs came within rc2f_band of rc^2 (rare) has its atom's list
+// walked again by the whole warp, one entry per lane.  Each lane recomputes
+// the pair's FP32 r^2 exactly as the walk did (same record, same operations)
+// and, for a pair near rc that FP64 decides otherwise, forms the term to take
+// out (counted by the walk) or to add (left out by it): force, half-list
+// partner, energy and virial alike.  The terms are summed over the warp into
+// the atom's first thread.  All 32 lanes call this together.
+template <int T, int Q, int MT, int HALF, int EV>
+__device__ __forceinline__ void fix_near_warp(const View &V, LJPair<MD_PREC_MIXED, MT, HALF, EV> &pr, bool flagged,
+                                              int gw, int lane, int tmode, const float4 *srec) {
+    constexpr int A = 32 / T;
+    unsigned m = __ballot_sync(0xffffffffu, flagged);
+    while (m) {
+        const int a = (__ffs(m) - 1) / T;  // the atom's index in the warp
+        m &= (T == 32) ? 0u : ~((((1u << (T & 31)) - 1u)) << (a * T));
+        const int p = gw * A + a;
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        const int cnt = V.ncount[p];
+        float xi, yi, zi;
+        int ti;
+        Pol<MD_PREC_MIXED>::load(V, p, xi, yi, zi, ti);
+        const float hx = R.hf[0], hy4 = R.hf[1] * 0.25f, hz16 = R.hf[2] * 0.0625f;
+        const uint32_t *base = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + a * T * Q;
+        float cx = 0.f, cy = 0.f, cz = 0.f, ce = 0.f, cw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = lane; k < cnt; k += 32) {
+            const uint32_t e = base[(size_t)(k / (T * Q)) * 32 * Q + (k % (T * Q))];
+            float xj, yj, zj;
+            int tj;
+            if (tmode == 1) {
+                const float4 r4 = srec[entry_j(e) & (kTileCap - 1)];
+                xj = r4.x; yj = r4.y; zj = r4.z; tj = __float_as_int(r4.w);
+            } else {
+                Pol<MD_PREC_MIXED>::load(V, entry_j(e), xj, yj, zj, tj);
+            }
+            const float dx = fmaf(-code_x(e), hx, xi - xj);
+            const float dy = fmaf(-code_y4(e), hy4, yi - yj);
+            const float dz = fmaf(-code_z16(e), hz16, zi - zj);
+            const float r2 = pair_r2(dx, dy, dz);
+            const float t = r2 - pr.rc2;
+            if (!(fabsf(t) < V.rc2f_band)) continue;
+            const bool exact = in_cut_fp64(V, p, e);
+            if (exact == (t < 0.f)) continue;
+            const float sgn = exact ? 1.f : -1.f;
+            const int tp = MT ? ti * pr.nt + tj : 0;
+            const float r2i = Pol<MD_PREC_MIXED>::rcp(r2);
+            const float r6i = r2i * r2i * r2i;
+            const float fpair = sgn * r6i * (pr.lj1[tp] * r6i - pr.lj2[tp]) * r2i;
+            const float fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
+            cx += fxp; cy += fyp; cz += fzp;
+            if (HALF) {
+                const int j = entry_j(e);
+                atomicAdd(&V.f[j], -(double)fxp);
+                atomicAdd(&V.f[pr.n + j], -(double)fyp);
+                atomicAdd(&V.f[2 * pr.n + j], -(double)fzp);
+            }
+            if (EV) {
+                const float wgt = HALF ? 1.f : 0.5f;
+                ce += sgn * wgt * (r6i * (pr.lj3[tp] * r6i - pr.lj4[tp]) - pr.off[tp]);
+                cw[0] += wgt * dx * fxp; cw[1] += wgt * dy * fyp; cw[2] += wgt * dz * fzp;
+                cw[3] += wgt * dx * fyp; cw[4] += wgt * dx * fzp; cw[5] += wgt * dy * fzp;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+            cz += __shfl_xor_sync(0xffffffffu, cz, o);
+            if (EV) {
+                ce += __shfl_xor_sync(0xffffffffu, ce, o);
+                for (int c = 0; c < 6; ++c) cw[c] += __shfl_xor_sync(0xffffffffu, cw[c], o);
+            }
+        }
+        if (lane == a * T) {
+            pr.ax.add(cx); pr.ay.add(cy); pr.az.add(cz);
+            if (EV) {
+                pr.e.add(ce);
+                for (int c = 0; c < 6; ++c) pr.w[c].add(cw[c]);
+            }
+        }
+    }
+}
+
+// registers per thread allowed to the mixed force-only pass: 56 keeps nine
+// 128-thread blocks (36 warps) resident per SM to hide the gather latency;
+// groups of 8+ threads and half lists with 4-entry loads take 64 (no spills),
+// the FP64 and energy/virial variants what they need
+template <int PREC, int T, int Q, int HALF, int EV>
+struct LjRegs {
+    static constexpr int value =
+        (PREC == MD_PREC_MIXED && !EV) ? (Q == 4 && (T > 4 || HALF) ? 64 : 56) : 255;
 };
 
 template <int PREC, int T, int Q, int HALF, int EV, int MT>
-__global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, KArgs a) {
+__global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
     __shared__ real s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
@@ -335,6 +450,7 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
     pr.nt = V.ntypes;
     pr.n = V.n_pad;
     pr.ti = 0;
+    pr.near_min = (real)3.0e38;
     pr.ax.zero(); pr.ay.zero(); pr.az.zero(); pr.e.zero();
     for (int k = 0; k < 6; ++k) pr.w[k].zero();
     bool valid = false;
@@ -348,6 +464,7 @@ __global__ void __launch_bounds__(256, LjOcc<PREC, Q, EV>::value) k_lj(View V, K
             const uint32_t *lp = V.nlist + (size_t)gw * (size_t)(A * V.maxneigh) + lane * Q;
             walk_mode<PREC, T, Q>(V, tmode, lp, sub, cnt, xi, yi, zi, R, s_rec, pr);
         }
+        if constexpr (PREC == MD_PREC_MIXED) fix_near_warp<T, Q>(V, pr, pr.near_min < V.rc2f_band, gw, lane, tmode, s_rec);
     }
     const double fx = group_sum<T>(pr.ax.value());
     const double fy = group_sum<T>(pr.ay.value());
@@ -406,6 +523,7 @@ __global__ void __launch_bounds__(128) k_lj_cells(View V, KArgs a) {
     pr.nt = V.ntypes;
     pr.n = V.n_pad;
     pr.ti = 0;
+    pr.near_min = 3.0e38f;  // no list entries here: FP32 cut-off decisions
     pr.ax.zero(); pr.ay.zero(); pr.az.zero();
     bool valid = false;
     if (p < V.n_pad && err == 0 && tmode >= 0) {

@@ -466,6 +466,19 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.rl2 = rl * rl;
     V.skin_half2 = 0.25 * h->cfg.skin * h->cfg.skin;
     V.rc2f = (float)V.rc2;
+    {
+        // A mixed pass's FP32 r^2 of a pair near rc is within
+        //   u rc (2 sqrt(3) (3 h + 2 skin + rc) + 4 rc),  u = 2^-24,
+        // of the FP64 value, h the largest bin edge: records |xr| <= h/2 + skin/2
+        // rounded to FP32, the FP32 bin edge, the difference, the fma, the three
+        // roundings of the sum of squares, and rc^2's own rounding.  Pairs within
+        // four times that of rc^2 get the FP64 cut-off decision.
+        double hmax = 0.0;
+        for (const Rep &R : h->reps)
+            for (int a = 0; a < 3; ++a) hmax = std::max(hmax, R.h[a]);
+        const double u = std::ldexp(1.0, -24), rc = h->cfg.cutoff;
+        V.rc2f_band = (float)(4.0 * u * rc * (2.0 * std::sqrt(3.0) * (3.0 * hmax + 2.0 * h->cfg.skin + rc) + 4.0 * rc));
+    }
     // FP32 list test margin: 1e-4 rl^2, ~50x the worst FP32 error of |d|^2
     V.rl2f_lo = (float)(V.rl2 * (1.0 - 1e-4));
     V.rl2f_hi = (float)(V.rl2 * (1.0 + 1e-4));

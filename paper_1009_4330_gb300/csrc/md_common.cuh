@@ -104,6 +104,7 @@ struct View {
     int ntypes;
     double dt, rc2, rl2, skin_half2;
     float rc2f, rl2f_lo, rl2f_hi, skin_half2f;
+    float rc2f_band;  // mixed LJ: |r^2 - rc^2| below this is decided in FP64 (force jump at rc)
     const Rep *rep;
     const int *tile_rep;
     const int *bin_rep;   // replica of each global bin

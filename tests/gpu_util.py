@@ -68,7 +68,7 @@ def margin_ok(x, box, rl, idx=None, margin=1e-9):
     return oracle.min_gap(x, box, rl, idx) > margin
 
 
-# FP32 resolves distances near rc only to ~1e-7 rc: a pair closer than this to
-# the cut-off may be counted differently from FP64 (the unshifted LJ force jumps
-# there), so mixed-precision force parity inputs keep pairs this far from rc
+# the general parity inputs keep every pair at least this far (relative) from
+# rc; pairs nearer rc, which the mixed pass decides in FP64, have their own
+# cases in test_gpu_cutoff.py
 RC_MARGIN_MIXED = 1e-6
