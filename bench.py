@@ -295,11 +295,11 @@ def run_reference(args, ws, rank):
 
 # DRAM traffic of the force kernel per atom, from the ncu capture summarised in
 # profiles/k_lj_lj500k_mixed_full.md (the md_step form of the pass:
-# dram__bytes_read.sum + dram__bytes_write.sum = 182.10 + 4.33 MB for 500,000
+# dram__bytes_read.sum + dram__bytes_write.sum = 182.09 + 4.45 MB for 500,000
 # atoms; scaled by atoms, the list length per atom being the same).  Valid for
 # that variant only: T = 1 thread per atom, Q = 4, full list, 128-thread blocks,
 # records gathered (no staging).
-K_LJ_TRAFFIC_PER_ATOM = (182.098176e6 + 4.329472e6) / 500000
+K_LJ_TRAFFIC_PER_ATOM = (182.090752e6 + 4.451840e6) / 500000
 K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full", "block": 128, "tile_atoms": 0}
 
 
