@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--block", type=int, default=128, help="force-kernel threads per block when --tpa is given")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
-    ap.add_argument("--profile", default=None, choices=["build", "eam_backward"],
+    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch"],
                     help="run one small workload for a profiler and exit: 'build' = LJ liquid (--cells, --rc), "
                          "100 steps to melt the lattice, then two list rebuilds; 'eam_backward' = EAM metal "
                          "(--cells), forces + backward twice")
@@ -536,12 +536,22 @@ def run_profile(args):
     """Small workloads for profiler captures (not a bench line)."""
     import torch
     import synth
-    from paper_1009_4330_gb300 import System
+    from paper_1009_4330_gb300 import System, lj_params
     if args.profile == "build":
         s, d = make_lj(synth, args.cells, args.rc, "mixed", tpa=args.tpa or (1 if args.rc < 3 else 4), lst="full")
         s.step(100)
         s.build_neighbors()
         s.build_neighbors()
+    elif args.profile == "batch":
+        # the 512-replica batch: graph steps, then eager steps (kernels visible to a profiler)
+        b = synth.config4()
+        natoms = int(sum(b["sizes"]))
+        s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
+                         precision="mixed", tpa=args.tpa or 1)
+        s.step(50)
+        ms_graph, _, _, _ = time_steps(s, 50, 5)
+        ms_eager, _, _, _ = time_steps(s, 20, 2, eager=True)
+        print(json.dumps({"ms_per_step_graph": ms_graph / 50, "ms_per_step_eager": ms_eager / 20}))
     else:
         d = synth.config2(cells=args.cells, displacement=0.1)
         s = System.eam(d["x"], d["v"], d["box"], eam_params=d["eam"], skin=d["skin"], dt=d["dt"], mass=d["mass"],
@@ -550,8 +560,10 @@ def run_profile(args):
         for _ in range(2):
             s.compute_forces()
             s.backward(g)
+    if args.profile != "batch":
+        natoms = int(d["x"].shape[0])
     torch.cuda.synchronize()
-    print(json.dumps({"profile": args.profile, "atoms": int(d["x"].shape[0]), "info": s.info()}))
+    print(json.dumps({"profile": args.profile, "atoms": natoms, "info": s.info()}))
     s.close()
 
 

@@ -470,7 +470,8 @@ constexpr int kBatch = 14;  // rounds whose list entries are appended together
 constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
 
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(View V, KArgs a) {
+__device__ __forceinline__ void build_cell(const View &V, int gb, int part, int lane, int w, int &my_max,
+                                           long long &my_sum) {
     __shared__ float4 s_h[kBuildWarps][32];
     __shared__ float4 s_q[kBuildWarps][kQueue];  // shifted candidate position, .w = list entry bits
     __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
@@ -478,6 +479,266 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     __shared__ int s_delta[kBuildWarps][2][64];     // per tile of the chunk, per stencil code: entry shift
     __shared__ uint32_t s_t[kBuildWarps][kBatch][32];  // per round: home atom's mask of accepted candidates
     __shared__ uint32_t s_e[kBuildWarps][kBatch][32];  // per round: candidate's list entry
+    const int r = V.bin_rep[gb];
+    const Rep &R = V.rep[r];
+    const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
+    const int la = 5 - lt, ltq = lt + lq, tq = 1 << ltq;
+    const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
+    const int xyz = V.bin2xyz[gb];
+    const int bx = unpack_bx(xyz), by = unpack_by(xyz), bz = unpack_bz(xyz);
+    const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
+    // neighbour cell (row = lane / 3, dx = lane % 3 - 1) bounds, one lane each
+    if (lane < 27) {
+        const int row = lane / 3;
+        const int dx = lane - 3 * row - 1, dy = row % 3 - 1, dz = row / 3 - 1;
+        int cx = bx + dx, cy = by + dy, cz = bz + dz;
+        cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
+        cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
+        cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
+        const int nbin = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
+        s_cell[w][lane] = make_int2(V.bin_start[nbin], V.bin_count[nbin]);
+    }
+    const int hs = V.bin_start[gb], hn = V.bin_count[gb];
+    const float rl2f = 0.5f * (V.rl2f_lo + V.rl2f_hi), margin = 0.5f * (V.rl2f_hi - V.rl2f_lo);
+    // box pre-test bound: above every squared distance the margin band can hold
+    const float keep2 = V.rl2f_hi + margin;
+    for (int h0 = 32 * part; h0 < hn; h0 += 32 * V.hsplit) {
+        const int nh = min(32, hn - h0);
+        const int hbase = hs + h0;  // slot of home atom 0 of this chunk
+        __syncwarp();
+        {
+            // home record with |r|^2 in .w; padding far away (never accepted, never in the band)
+            float4 hr = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
+            if (lane < nh) hr = V.rec[hbase + lane];
+            hr.w = hr.x * hr.x + hr.y * hr.y + hr.z * hr.z;
+            s_h[w][lane] = hr;
+            // bounding box of the chunk's home atoms
+            const bool in = lane < nh;
+            float lox = in ? hr.x : 3.0e38f, hix = in ? hr.x : -3.0e38f;
+            float loy, loz, hiy, hiz;
+            loy = in ? hr.y : 3.0e38f; hiy = in ? hr.y : -3.0e38f;
+            loz = in ? hr.z : 3.0e38f; hiz = in ? hr.z : -3.0e38f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+                loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+                loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
+                hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+                hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+                hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
+            }
+            if (lane == 0) {
+                s_box[w][0] = make_float4(lox, loy, loz, 0.f);
+                s_box[w][1] = make_float4(hix, hiy, hiz, 0.f);
+            }
+        }
+        // Block-local entries: the chunk's atoms lie in one or two tiles; for
+        // each, stencil cell k's records start at tile_off[k] in the tile's
+        // staging, so a candidate's entry j<<6|code becomes
+        // (j - cell start + tile_off[k])<<6|code: a shift per (tile, code).
+        const int tpa_atoms = V.tile_atoms;
+        const int tA = tpa_atoms ? hbase / tpa_atoms : 0;
+        const int tB = tpa_atoms ? (hbase + nh - 1) / tpa_atoms : 0;
+        if (lane < 27) {
+            const int row = lane / 3;
+            const int ox = lane - 3 * row - 1, oy = row % 3 - 1, oz = row / 3 - 1;
+            const int code = ((oz + 1) << 4) | ((oy + 1) << 2) | (ox + 1);
+            for (int X = 0; X < 2; ++X) {
+                int delta = 0;
+                const int t = X ? tB : tA;
+                if (tpa_atoms && V.tile_cnt[t] >= 0) {
+                    const int4 b = V.tile_box[t];
+                    const int bdx = b.w & 0xffff, bdy = b.w >> 16;
+                    int idx = (bx + ox - b.x) + bdx * ((by + oy - b.y) + bdy * (bz + oz - b.z));
+                    idx = min(max(idx, 0), kTileBox - 1);
+                    const unsigned wd = V.tile_bits[(size_t)t * 32 + (idx >> 5)];
+                    int k = V.tile_wpre[(size_t)t * 32 + (idx >> 5)] + __popc(wd & ((1u << (idx & 31)) - 1u));
+                    k = min(k, kTileCells - 1);
+                    delta = (V.tile_off[(size_t)t * kTileCells + k] - s_cell[w][lane].x) * 64;
+                }
+                s_delta[w][X][code] = delta;
+            }
+        }
+        __syncwarp();
+        // this lane as a home atom: its list
+        const int p = hbase + lane;
+        const int tsel = (tpa_atoms && p / tpa_atoms != tA) ? 1 : 0;
+        uint32_t *const lbase = V.nlist + (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
+        unsigned slot = 0u;  // offset from lbase
+        const int jump = (32 << lq) - (tq - 1);
+        int mycnt = 0;
+        int qn = 0;  // queued candidates (warp-uniform)
+        // append the batch's accepted candidates to the home atoms' lists,
+        // round by round in candidate order: each home-atom lane walks its
+        // own masks, so the loop runs as long as the longest share of the
+        // batch rather than the sum of each round's longest share
+        int rb = 0;      // rounds in the pending batch (warp-uniform)
+        unsigned nz = 0u;  // this home atom: rounds of the batch in which it accepts a candidate
+        auto append = [&]() {
+            __syncwarp();
+            int r = nz ? __ffs(nz) - 1 : rb;
+            unsigned t = r < rb ? s_t[w][r][lane] : 0u;
+            while (__any_sync(0xffffffffu, r < rb)) {
+                if (r < rb) {
+                    const uint32_t *row = &s_e[w][r][0];
+                    const int c1 = __ffs(t) - 1;
+                    t &= t - 1u;
+                    uint32_t e1 = row[c1];
+                    const bool two = t != 0u;  // a second entry from the same round
+                    uint32_t e2 = 0u;
+                    if (two) {
+                        e2 = row[__ffs(t) - 1];
+                        t &= t - 1u;
+                    }
+                    if (tpa_atoms) {
+                        e1 += (uint32_t)s_delta[w][tsel][e1 & 63u];
+                        e2 += (uint32_t)s_delta[w][tsel][e2 & 63u];
+                    }
+                    if (mycnt < maxn) lbase[slot] = e1;
+                    ++mycnt;
+                    slot += (mycnt & (tq - 1)) ? 1 : jump;
+                    if (two) {
+                        if (mycnt < maxn) lbase[slot] = e2;
+                        ++mycnt;
+                        slot += (mycnt & (tq - 1)) ? 1 : jump;
+                    }
+                    if (t == 0u) {  // next round with an accepted candidate
+                        const unsigned rest = nz & ~((2u << r) - 1u);
+                        r = rest ? __ffs(rest) - 1 : rb;
+                        if (r < rb) t = s_t[w][r][lane];
+                    }
+                }
+            }
+            __syncwarp();
+            rb = 0;
+            nz = 0u;
+        };
+        // one round: queue entries 0..cnt-1 (cnt <= 32), one per lane
+        auto round = [&](int cnt) {
+            float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
+            uint32_t e = 0u;
+            if (lane < cnt) {
+                const float4 c = s_q[w][lane];
+                qx = c.x; qy = c.y; qz = c.z;
+                e = __float_as_uint(c.w);
+            }
+            // acceptance bits over the home atoms, 8 at a time with
+            // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
+            // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
+            // < ~1e-5 rl^2 here, far inside the margin); the sign bit of t
+            // is the decision, and the smallest |t| flags the margin band.
+            const float qx2 = -2.0f * qx, qy2 = -2.0f * qy, qz2 = -2.0f * qz;
+            const float q2m = qx * qx + qy * qy + qz * qz - rl2f;
+            unsigned acc = 0u;
+            float tmin = 3.0e38f;
+            // home atoms from the top down, 8 at a time: each test shifts its
+            // sign bit in at bit 0, so that home atom h ends at bit h
+#pragma unroll 1
+            for (int hb = (nh - 1) & ~7; hb >= 0; hb -= 8) {
+                float t8[8];
+#pragma unroll
+                for (int k = 7; k >= 0; --k) {
+                    const float4 ri = s_h[w][hb + k];
+                    t8[k] = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                    acc = __funnelshift_l(__float_as_uint(t8[k]), acc, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) tmin = fmin3(tmin, fabsf(t8[k]), fabsf(t8[k + 1]));
+            }
+            const int j = (int)(e >> 6);
+            if (tmin < margin) {  // margin band: decide those pairs in FP64 (rare)
+                for (int h = 0; h < nh; ++h) {
+                    const float4 ri = s_h[w][h];
+                    const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
+                    if (fabsf(t) < margin) {
+                        const bool in = in_list_fp64<PREC>(V, R, hbase + h, j, entry_dx(e), entry_dy(e),
+                                                            entry_dz(e));
+                        acc = in ? (acc | (1u << h)) : (acc & ~(1u << h));
+                    }
+                }
+            }
+            // exclusions: the atom itself; for HALF every home atom with slot >= j
+            const int jh = j - hbase;  // j as a home-atom index, if it is one
+            if ((e & 63u) == 21u && jh >= 0 && jh < 32) acc &= ~(1u << jh);
+            if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
+            // lane = home atom: bit c set if candidate lane c is accepted;
+            // kept with the round's entries until the batch is appended
+            const unsigned tr = warp_transpose32(acc, lane);
+            s_t[w][rb][lane] = tr;
+            s_e[w][rb][lane] = e;
+            nz |= (tr != 0u ? 1u : 0u) << rb;
+            if (++rb == kBatch) append();
+        };
+        // fill the queue from the rows in order until it holds a full
+        // round (or the rows are done), then run the round
+        int row = 0, c0 = 0;
+        int m = s_cell[w][0].y + s_cell[w][1].y + s_cell[w][2].y;
+#pragma unroll 1
+        while (true) {
+#pragma unroll 1
+            while (qn < 32 && row < 9) {
+                // this lane as a candidate, shifted into the home frame,
+                // kept if within rl (plus the band) of the home bounding box
+                const int f = c0 + lane;
+                bool keep = false;
+                float4 c;
+                if (f < m) {
+                    const int dy = row % 3 - 1, dz = row / 3 - 1;
+                    const int2 c0_ = s_cell[w][3 * row], c1_ = s_cell[w][3 * row + 1];
+                    const int seg = (f >= c0_.y) + (f >= c0_.y + c1_.y);
+                    const int j = seg == 0 ? c0_.x + f
+                                           : (seg == 1 ? c1_.x + f - c0_.y
+                                                       : s_cell[w][3 * row + 2].x + f - c0_.y - c1_.y);
+                    const float4 rj = V.rec[j];
+                    c.x = rj.x + (seg - 1) * hx;
+                    c.y = rj.y + dy * hy;
+                    c.z = rj.z + dz * hz;
+                    c.w = __uint_as_float(((uint32_t)j << 6) | (uint32_t)seg | ((uint32_t)(dz + 1) << 4) |
+                                          ((uint32_t)(dy + 1) << 2));
+                    const float4 lo = s_box[w][0], hi = s_box[w][1];
+                    const float bx_ = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
+                    const float by_ = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
+                    const float bz_ = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
+                    keep = bx_ * bx_ + by_ * by_ + bz_ * bz_ < keep2;
+                }
+                const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                if (keep) s_q[w][qn + __popc(kb & ((1u << lane) - 1u))] = c;
+                qn += __popc(kb);
+                c0 += 32;
+                if (c0 >= m) {
+                    c0 = 0;
+                    ++row;
+                    if (row < 9)
+                        m = s_cell[w][3 * row].y + s_cell[w][3 * row + 1].y + s_cell[w][3 * row + 2].y;
+                }
+            }
+            if (qn == 0) break;
+            const int cnt = min(qn, 32);
+            __syncwarp();
+            round(cnt);
+            qn -= cnt;
+            __syncwarp();
+            float4 rest;
+            if (lane < qn) rest = s_q[w][32 + lane];
+            __syncwarp();
+            if (lane < qn) s_q[w][lane] = rest;
+            __syncwarp();
+        }
+        if (rb > 0) append();
+        if (lane < nh) {
+            V.ncount[p] = min(mycnt, maxn);
+            if (mycnt > maxn) {
+                atomicMax(&V.ctl->need_maxneigh, mycnt);
+                latch_error(V.ctl, kErrOverflow);
+            }
+            my_max = max(my_max, mycnt);
+            my_sum += mycnt;
+        }
+    }
+}
+
+template <int PREC, int HALF>
+__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(View V, KArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
     const int gw = blockIdx.x * kBuildWarps + w;
@@ -488,263 +749,7 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     if (gb < V.nbins_total) {
         const int r = V.bin_rep[gb];
         my_rep = r;
-        if (a.all || V.rep_flag[r]) {
-            const Rep &R = V.rep[r];
-            const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
-            const int la = 5 - lt, ltq = lt + lq, tq = 1 << ltq;
-            const int nbx = R.nb[0], nby = R.nb[1], nbz = R.nb[2];
-            const int xyz = V.bin2xyz[gb];
-            const int bx = unpack_bx(xyz), by = unpack_by(xyz), bz = unpack_bz(xyz);
-            const float hx = R.hf[0], hy = R.hf[1], hz = R.hf[2];
-            // neighbour cell (row = lane / 3, dx = lane % 3 - 1) bounds, one lane each
-            if (lane < 27) {
-                const int row = lane / 3;
-                const int dx = lane - 3 * row - 1, dy = row % 3 - 1, dz = row / 3 - 1;
-                int cx = bx + dx, cy = by + dy, cz = bz + dz;
-                cx += (cx < 0) ? nbx : ((cx >= nbx) ? -nbx : 0);
-                cy += (cy < 0) ? nby : ((cy >= nby) ? -nby : 0);
-                cz += (cz < 0) ? nbz : ((cz >= nbz) ? -nbz : 0);
-                const int nbin = V.lin2bin[R.bin0 + (cz * nby + cy) * nbx + cx];
-                s_cell[w][lane] = make_int2(V.bin_start[nbin], V.bin_count[nbin]);
-            }
-            const int hs = V.bin_start[gb], hn = V.bin_count[gb];
-            const float rl2f = 0.5f * (V.rl2f_lo + V.rl2f_hi), margin = 0.5f * (V.rl2f_hi - V.rl2f_lo);
-            // box pre-test bound: above every squared distance the margin band can hold
-            const float keep2 = V.rl2f_hi + margin;
-            for (int h0 = 32 * part; h0 < hn; h0 += 32 * V.hsplit) {
-                const int nh = min(32, hn - h0);
-                const int hbase = hs + h0;  // slot of home atom 0 of this chunk
-                __syncwarp();
-                {
-                    // home record with |r|^2 in .w; padding far away (never accepted, never in the band)
-                    float4 hr = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
-                    if (lane < nh) hr = V.rec[hbase + lane];
-                    hr.w = hr.x * hr.x + hr.y * hr.y + hr.z * hr.z;
-                    s_h[w][lane] = hr;
-                    // bounding box of the chunk's home atoms
-                    const bool in = lane < nh;
-                    float lox = in ? hr.x : 3.0e38f, hix = in ? hr.x : -3.0e38f;
-                    float loy, loz, hiy, hiz;
-                    loy = in ? hr.y : 3.0e38f; hiy = in ? hr.y : -3.0e38f;
-                    loz = in ? hr.z : 3.0e38f; hiz = in ? hr.z : -3.0e38f;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-                        loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-                        loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
-                        hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-                        hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
-                        hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
-                    }
-                    if (lane == 0) {
-                        s_box[w][0] = make_float4(lox, loy, loz, 0.f);
-                        s_box[w][1] = make_float4(hix, hiy, hiz, 0.f);
-                    }
-                }
-                // Block-local entries: the chunk's atoms lie in one or two tiles; for
-                // each, stencil cell k's records start at tile_off[k] in the tile's
-                // staging, so a candidate's entry j<<6|code becomes
-                // (j - cell start + tile_off[k])<<6|code: a shift per (tile, code).
-                const int tpa_atoms = V.tile_atoms;
-                const int tA = tpa_atoms ? hbase / tpa_atoms : 0;
-                const int tB = tpa_atoms ? (hbase + nh - 1) / tpa_atoms : 0;
-                if (lane < 27) {
-                    const int row = lane / 3;
-                    const int ox = lane - 3 * row - 1, oy = row % 3 - 1, oz = row / 3 - 1;
-                    const int code = ((oz + 1) << 4) | ((oy + 1) << 2) | (ox + 1);
-                    for (int X = 0; X < 2; ++X) {
-                        int delta = 0;
-                        const int t = X ? tB : tA;
-                        if (tpa_atoms && V.tile_cnt[t] >= 0) {
-                            const int4 b = V.tile_box[t];
-                            const int bdx = b.w & 0xffff, bdy = b.w >> 16;
-                            int idx = (bx + ox - b.x) + bdx * ((by + oy - b.y) + bdy * (bz + oz - b.z));
-                            idx = min(max(idx, 0), kTileBox - 1);
-                            const unsigned wd = V.tile_bits[(size_t)t * 32 + (idx >> 5)];
-                            int k = V.tile_wpre[(size_t)t * 32 + (idx >> 5)] + __popc(wd & ((1u << (idx & 31)) - 1u));
-                            k = min(k, kTileCells - 1);
-                            delta = (V.tile_off[(size_t)t * kTileCells + k] - s_cell[w][lane].x) * 64;
-                        }
-                        s_delta[w][X][code] = delta;
-                    }
-                }
-                __syncwarp();
-                // this lane as a home atom: its list
-                const int p = hbase + lane;
-                const int tsel = (tpa_atoms && p / tpa_atoms != tA) ? 1 : 0;
-                uint32_t *const lbase = V.nlist + (size_t)(p >> la) * (size_t)((1 << la) * maxn) + (size_t)((p & ((1 << la) - 1)) << ltq);
-                unsigned slot = 0u;  // offset from lbase
-                const int jump = (32 << lq) - (tq - 1);
-                int mycnt = 0;
-                int qn = 0;  // queued candidates (warp-uniform)
-                // append the batch's accepted candidates to the home atoms' lists,
-                // round by round in candidate order: each home-atom lane walks its
-                // own masks, so the loop runs as long as the longest share of the
-                // batch rather than the sum of each round's longest share
-                int rb = 0;      // rounds in the pending batch (warp-uniform)
-                unsigned nz = 0u;  // this home atom: rounds of the batch in which it accepts a candidate
-                auto append = [&]() {
-                    __syncwarp();
-                    int r = nz ? __ffs(nz) - 1 : rb;
-                    unsigned t = r < rb ? s_t[w][r][lane] : 0u;
-                    while (__any_sync(0xffffffffu, r < rb)) {
-                        if (r < rb) {
-                            const uint32_t *row = &s_e[w][r][0];
-                            const int c1 = __ffs(t) - 1;
-                            t &= t - 1u;
-                            uint32_t e1 = row[c1];
-                            const bool two = t != 0u;  // a second entry from the same round
-                            uint32_t e2 = 0u;
-                            if (two) {
-                                e2 = row[__ffs(t) - 1];
-                                t &= t - 1u;
-                            }
-                            if (tpa_atoms) {
-                                e1 += (uint32_t)s_delta[w][tsel][e1 & 63u];
-                                e2 += (uint32_t)s_delta[w][tsel][e2 & 63u];
-                            }
-                            if (mycnt < maxn) lbase[slot] = e1;
-                            ++mycnt;
-                            slot += (mycnt & (tq - 1)) ? 1 : jump;
-                            if (two) {
-                                if (mycnt < maxn) lbase[slot] = e2;
-                                ++mycnt;
-                                slot += (mycnt & (tq - 1)) ? 1 : jump;
-                            }
-                            if (t == 0u) {  // next round with an accepted candidate
-                                const unsigned rest = nz & ~((2u << r) - 1u);
-                                r = rest ? __ffs(rest) - 1 : rb;
-                                if (r < rb) t = s_t[w][r][lane];
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    rb = 0;
-                    nz = 0u;
-                };
-                // one round: queue entries 0..cnt-1 (cnt <= 32), one per lane
-                auto round = [&](int cnt) {
-                    float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
-                    uint32_t e = 0u;
-                    if (lane < cnt) {
-                        const float4 c = s_q[w][lane];
-                        qx = c.x; qy = c.y; qz = c.z;
-                        e = __float_as_uint(c.w);
-                    }
-                    // acceptance bits over the home atoms, 8 at a time with
-                    // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
-                    // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
-                    // < ~1e-5 rl^2 here, far inside the margin); the sign bit of t
-                    // is the decision, and the smallest |t| flags the margin band.
-                    const float qx2 = -2.0f * qx, qy2 = -2.0f * qy, qz2 = -2.0f * qz;
-                    const float q2m = qx * qx + qy * qy + qz * qz - rl2f;
-                    unsigned acc = 0u;
-                    float tmin = 3.0e38f;
-                    // home atoms from the top down, 8 at a time: each test shifts its
-                    // sign bit in at bit 0, so that home atom h ends at bit h
-#pragma unroll 1
-                    for (int hb = (nh - 1) & ~7; hb >= 0; hb -= 8) {
-                        float t8[8];
-#pragma unroll
-                        for (int k = 7; k >= 0; --k) {
-                            const float4 ri = s_h[w][hb + k];
-                            t8[k] = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
-                            acc = __funnelshift_l(__float_as_uint(t8[k]), acc, 1);
-                        }
-#pragma unroll
-                        for (int k = 0; k < 8; k += 2) tmin = fmin3(tmin, fabsf(t8[k]), fabsf(t8[k + 1]));
-                    }
-                    const int j = (int)(e >> 6);
-                    if (tmin < margin) {  // margin band: decide those pairs in FP64 (rare)
-                        for (int h = 0; h < nh; ++h) {
-                            const float4 ri = s_h[w][h];
-                            const float t = fmaf(qx2, ri.x, fmaf(qy2, ri.y, fmaf(qz2, ri.z, ri.w + q2m)));
-                            if (fabsf(t) < margin) {
-                                const bool in = in_list_fp64<PREC>(V, R, hbase + h, j, entry_dx(e), entry_dy(e),
-                                                                    entry_dz(e));
-                                acc = in ? (acc | (1u << h)) : (acc & ~(1u << h));
-                            }
-                        }
-                    }
-                    // exclusions: the atom itself; for HALF every home atom with slot >= j
-                    const int jh = j - hbase;  // j as a home-atom index, if it is one
-                    if ((e & 63u) == 21u && jh >= 0 && jh < 32) acc &= ~(1u << jh);
-                    if (HALF) acc &= jh <= 0 ? 0u : (jh >= 32 ? 0xffffffffu : ((1u << jh) - 1u));
-                    // lane = home atom: bit c set if candidate lane c is accepted;
-                    // kept with the round's entries until the batch is appended
-                    const unsigned tr = warp_transpose32(acc, lane);
-                    s_t[w][rb][lane] = tr;
-                    s_e[w][rb][lane] = e;
-                    nz |= (tr != 0u ? 1u : 0u) << rb;
-                    if (++rb == kBatch) append();
-                };
-                // fill the queue from the rows in order until it holds a full
-                // round (or the rows are done), then run the round
-                int row = 0, c0 = 0;
-                int m = s_cell[w][0].y + s_cell[w][1].y + s_cell[w][2].y;
-#pragma unroll 1
-                while (true) {
-#pragma unroll 1
-                    while (qn < 32 && row < 9) {
-                        // this lane as a candidate, shifted into the home frame,
-                        // kept if within rl (plus the band) of the home bounding box
-                        const int f = c0 + lane;
-                        bool keep = false;
-                        float4 c;
-                        if (f < m) {
-                            const int dy = row % 3 - 1, dz = row / 3 - 1;
-                            const int2 c0_ = s_cell[w][3 * row], c1_ = s_cell[w][3 * row + 1];
-                            const int seg = (f >= c0_.y) + (f >= c0_.y + c1_.y);
-                            const int j = seg == 0 ? c0_.x + f
-                                                   : (seg == 1 ? c1_.x + f - c0_.y
-                                                               : s_cell[w][3 * row + 2].x + f - c0_.y - c1_.y);
-                            const float4 rj = V.rec[j];
-                            c.x = rj.x + (seg - 1) * hx;
-                            c.y = rj.y + dy * hy;
-                            c.z = rj.z + dz * hz;
-                            c.w = __uint_as_float(((uint32_t)j << 6) | (uint32_t)seg | ((uint32_t)(dz + 1) << 4) |
-                                                  ((uint32_t)(dy + 1) << 2));
-                            const float4 lo = s_box[w][0], hi = s_box[w][1];
-                            const float bx_ = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
-                            const float by_ = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
-                            const float bz_ = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
-                            keep = bx_ * bx_ + by_ * by_ + bz_ * bz_ < keep2;
-                        }
-                        const unsigned kb = __ballot_sync(0xffffffffu, keep);
-                        if (keep) s_q[w][qn + __popc(kb & ((1u << lane) - 1u))] = c;
-                        qn += __popc(kb);
-                        c0 += 32;
-                        if (c0 >= m) {
-                            c0 = 0;
-                            ++row;
-                            if (row < 9)
-                                m = s_cell[w][3 * row].y + s_cell[w][3 * row + 1].y + s_cell[w][3 * row + 2].y;
-                        }
-                    }
-                    if (qn == 0) break;
-                    const int cnt = min(qn, 32);
-                    __syncwarp();
-                    round(cnt);
-                    qn -= cnt;
-                    __syncwarp();
-                    float4 rest;
-                    if (lane < qn) rest = s_q[w][32 + lane];
-                    __syncwarp();
-                    if (lane < qn) s_q[w][lane] = rest;
-                    __syncwarp();
-                }
-                if (rb > 0) append();
-                if (lane < nh) {
-                    V.ncount[p] = min(mycnt, maxn);
-                    if (mycnt > maxn) {
-                        atomicMax(&V.ctl->need_maxneigh, mycnt);
-                        latch_error(V.ctl, kErrOverflow);
-                    }
-                    my_max = max(my_max, mycnt);
-                    my_sum += mycnt;
-                }
-            }
-        }
+        if (a.all || V.rep_flag[r]) build_cell<PREC, HALF>(V, gb, part, lane, w, my_max, my_sum);
     }
     // statistics per replica: warp max / sum, merged over the block's warps
     // that belong to the same replica, one atomic per run
@@ -783,6 +788,70 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     }
 }
 
+// Work list of a batched rebuild: the replicas flagged by the drift, each with
+// its first (bin, part) unit in a flat numbering and its first global bin.
+// One block: exclusive scans over the replicas, a block's width at a time.
+__global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
+    __shared__ int s_warp[32];
+    int base_u = 0, base_n = 0;
+    for (int q0 = 0; q0 < V.n_rep; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const bool f = q < V.n_rep && (a.all || V.rep_flag[q]);
+        const int units = f ? V.rep[q].nbins * V.hsplit : 0;
+        int tot_u, tot_n;
+        const int eu = block_excl_scan(units, s_warp, &tot_u);
+        const int en = block_excl_scan(f ? 1 : 0, s_warp, &tot_n);
+        if (f) {
+            V.wl_u0[base_n + en] = base_u + eu;
+            V.wl_bin[base_n + en] = V.rep[q].bin0;
+        }
+        base_u += tot_u;
+        base_n += tot_n;
+    }
+    if (threadIdx.x == 0) {
+        V.wl_u0[base_n] = base_u;
+        *V.wl_n = base_n;
+    }
+}
+
+// Batched rebuild: a fixed grid walks the work list's units (k_worklist), so
+// that the bins of replicas keeping their lists cost no block launches.
+template <int PREC, int HALF>
+__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build_wl(View V, KArgs a) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nf = *V.wl_n;
+    const int total = V.wl_u0[nf];
+    for (int u = blockIdx.x * kBuildWarps + w; u < total; u += gridDim.x * kBuildWarps) {
+        // the flagged replica holding unit u: the last f with wl_u0[f] <= u
+        int lo = 0, hi = nf - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&V.wl_u0[mid]) <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const int local = u - __ldg(&V.wl_u0[lo]);
+        const int gb = __ldg(&V.wl_bin[lo]) + local / V.hsplit, part = local % V.hsplit;
+        int my_max = 0;
+        long long my_sum = 0;
+        build_cell<PREC, HALF>(V, gb, part, lane, w, my_max, my_sum);
+        for (int o = 16; o > 0; o >>= 1) {
+            my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+            my_sum += __shfl_xor_sync(0xffffffffu, my_sum, o);
+        }
+        if (lane == 0 && my_sum > 0) {
+            const int r = V.bin_rep[gb];
+            atomicMax(&V.rep_maxcnt[r], my_max);
+            atomicAdd(&V.rep_entries[r], (unsigned long long)my_sum);
+        }
+    }
+    if (last_block(&V.ctl->ticket_build)) {
+        if (threadIdx.x == 0) {
+            V.ctl->ticket_build = 0;
+            V.ctl->rebuilds += nf;
+        }
+    }
+}
+
 // ------------------------------------------------------------- dispatch ----
 
 void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &seq) {
@@ -805,11 +874,17 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
                         dim3(nb), dim3(256), 0, a});
     if (V.tile_atoms > 0)
         seq.push_back(KCall{(const void *)k_tiles, dim3((V.n_ftiles + 3) / 4), dim3(128), 0, a});
-    const void *kb;
-    if (V.prec == MD_PREC_FP64)
-        kb = V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>;
-    else
-        kb = V.half ? (const void *)k_build<MD_PREC_MIXED, 1> : (const void *)k_build<MD_PREC_MIXED, 0>;
+    const bool fp64 = V.prec == MD_PREC_FP64;
+    if (V.n_rep > 1 && !all) {
+        // a batch rebuilding some of its replicas: list their bins, fixed grid
+        const void *kb = fp64 ? (V.half ? (const void *)k_build_wl<MD_PREC_FP64, 1> : (const void *)k_build_wl<MD_PREC_FP64, 0>)
+                              : (V.half ? (const void *)k_build_wl<MD_PREC_MIXED, 1> : (const void *)k_build_wl<MD_PREC_MIXED, 0>);
+        seq.push_back(KCall{(const void *)k_worklist, dim3(1), dim3(1024), 0, a});
+        seq.push_back(KCall{kb, dim3(V.n_sm * (32 / kBuildWarps)), dim3(32 * kBuildWarps), 0, a});
+        return;
+    }
+    const void *kb = fp64 ? (V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>)
+                          : (V.half ? (const void *)k_build<MD_PREC_MIXED, 1> : (const void *)k_build<MD_PREC_MIXED, 0>);
     seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + kBuildWarps - 1) / kBuildWarps), dim3(32 * kBuildWarps), 0, a});
 }
 

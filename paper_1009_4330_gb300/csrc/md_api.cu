@@ -555,6 +555,15 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.ev, 8 * n);
     AL(h->d_tab, 1);
     AL(h->d_ctl, 1);
+    AL(V.wl_u0, (size_t)n_rep + 1);
+    AL(V.wl_bin, (size_t)n_rep);
+    AL(V.wl_n, 1);
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+        V.n_sm = nsm;
+    }
 #undef AL
     V.tab = h->d_tab;
     V.ctl = h->d_ctl;

@@ -129,6 +129,10 @@ struct View {
     // list
     uint32_t *nlist;
     int *ncount;
+    // batched rebuild work list (k_worklist): per flagged replica, its first
+    // (bin, part) unit in a flat numbering [n_flagged + 1] and its first bin
+    int *wl_u0, *wl_bin, *wl_n;
+    int n_sm;             // SMs of the device (fixed grids)
     // EAM
     double *fp64;         // F'(rho) per atom (fp64 path)
     float *fp32;          // F'(rho) per atom (mixed path)
