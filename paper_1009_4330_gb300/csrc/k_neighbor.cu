@@ -34,9 +34,7 @@ __global__ void k_zero_bins(View V, KArgs a) {
 // a.mode = 1: absolute positions/velocities/types/ids are already staged in
 // the scratch arrays (creation, set_state): wrap into the box and bin.
 template <int PREC>
-__global__ void k_prepare(View V, KArgs a) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.n_pad) return;
+__device__ __forceinline__ void prepare_slot(const View &V, const KArgs &a, int p) {
     const int r = V.tile_rep[p >> 5];
     if (!a.all && !V.rep_flag[r]) return;
     const Rep &R = V.rep[r];
@@ -108,6 +106,35 @@ __global__ void k_prepare(View V, KArgs a) {
     if (lane == leader) base = atomicAdd(&V.bin_count[gb], __popc(same));
     base = __shfl_sync(same, base, leader);
     V.slot[p] = base + rank;
+}
+
+// Flat slot numbering of the batched rebuild's work list: unit u -> slot.
+__device__ __forceinline__ int wl_slot(const View &V, int nf, int u) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&V.wl_s0[mid]) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return __ldg(&V.wl_a0[lo]) + (u - __ldg(&V.wl_s0[lo]));
+}
+
+// the slots of one rebuild pass: every slot, or (a.wl) the work list's
+#define FOR_REBUILD_SLOTS(p, body)                                                                  \
+    if (a.wl) {                                                                                     \
+        const int nf_ = *V.wl_n, total_ = V.wl_s0[nf_];                                             \
+        for (int u_ = blockIdx.x * blockDim.x + threadIdx.x; u_ < total_; u_ += gridDim.x * blockDim.x) { \
+            const int p = wl_slot(V, nf_, u_);                                                      \
+            body;                                                                                   \
+        }                                                                                           \
+    } else {                                                                                        \
+        const int p = blockIdx.x * blockDim.x + threadIdx.x;                                        \
+        if (p < V.n_pad) { body; }                                                                  \
+    }
+
+template <int PREC>
+__global__ void k_prepare(View V, KArgs a) {
+    FOR_REBUILD_SLOTS(p, prepare_slot<PREC>(V, a, p))
 }
 
 // Bins of a replica are numbered along a Morton (Z-order) curve through its
@@ -195,9 +222,7 @@ __global__ void k_scan3(View V, KArgs a) {
 
 // perm[bin_start[bin] + arrival slot] = old slot; sid = the atom ids in
 // the same (arrival) order, contiguous per bin for the ranking in k_gather
-__global__ void k_scatter(View V, KArgs a) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.n_pad) return;
+__device__ __forceinline__ void scatter_slot(const View &V, const KArgs &a, int p) {
     const int r = V.tile_rep[p >> 5];
     if (!a.all && !V.rep_flag[r]) return;
     if (p - V.rep[r].atom0 >= V.rep[r].natoms) return;
@@ -206,13 +231,15 @@ __global__ void k_scatter(View V, KArgs a) {
     V.sid[q] = V.tid[p];
 }
 
+__global__ void k_scatter(View V, KArgs a) {
+    FOR_REBUILD_SLOTS(p, scatter_slot(V, a, p))
+}
+
 // Final slot = bin start + rank of the atom's id inside its bin (so the
 // order does not depend on atomic arrival order); write the sorted state
 // (positions relative to the new bin centre), FP32 records, build reference.
 template <int PREC>
-__global__ void k_gather(View V, KArgs a) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= V.n_pad) return;
+__device__ __forceinline__ void gather_slot(const View &V, const KArgs &a, int q) {
     const int r = V.tile_rep[q >> 5];
     if (!a.all && !V.rep_flag[r]) return;
     const Rep &R = V.rep[r];
@@ -254,6 +281,11 @@ __global__ void k_gather(View V, KArgs a) {
     const float4 rr = make_float4((float)xr[0], (float)xr[1], (float)xr[2], __int_as_float(t));
     V.rec[dst] = rr;
     V.recb[dst] = rr;
+}
+
+template <int PREC>
+__global__ void k_gather(View V, KArgs a) {
+    FOR_REBUILD_SLOTS(q, gather_slot<PREC>(V, a, q))
 }
 
 // global bin of slot p (after the gather)
@@ -789,27 +821,34 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
 }
 
 // Work list of a batched rebuild: the replicas flagged by the drift, each with
-// its first (bin, part) unit in a flat numbering and its first global bin.
-// One block: exclusive scans over the replicas, a block's width at a time.
+// its first (bin, part) unit and its first slot in flat numberings, its first
+// global bin and its first slot.  One block: exclusive scans over the
+// replicas, a block's width at a time.
 __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
     __shared__ int s_warp[32];
-    int base_u = 0, base_n = 0;
+    int base_u = 0, base_s = 0, base_n = 0;
     for (int q0 = 0; q0 < V.n_rep; q0 += blockDim.x) {
         const int q = q0 + threadIdx.x;
         const bool f = q < V.n_rep && (a.all || V.rep_flag[q]);
         const int units = f ? V.rep[q].nbins * V.hsplit : 0;
-        int tot_u, tot_n;
+        const int slots = f ? V.rep[q].ntiles * 32 : 0;
+        int tot_u, tot_s, tot_n;
         const int eu = block_excl_scan(units, s_warp, &tot_u);
+        const int es = block_excl_scan(slots, s_warp, &tot_s);
         const int en = block_excl_scan(f ? 1 : 0, s_warp, &tot_n);
         if (f) {
             V.wl_u0[base_n + en] = base_u + eu;
             V.wl_bin[base_n + en] = V.rep[q].bin0;
+            V.wl_s0[base_n + en] = base_s + es;
+            V.wl_a0[base_n + en] = V.rep[q].atom0;
         }
         base_u += tot_u;
+        base_s += tot_s;
         base_n += tot_n;
     }
     if (threadIdx.x == 0) {
         V.wl_u0[base_n] = base_u;
+        V.wl_s0[base_n] = base_s;
         *V.wl_n = base_n;
     }
 }
@@ -857,29 +896,31 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build_wl
 void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &seq) {
     KArgs a{};
     a.all = all ? 1 : 0;
-    const int nb = (V.n_pad + 255) / 256;
+    const bool fp64 = V.prec == MD_PREC_FP64;
+    // a batch rebuilding some of its replicas: list them first, then the
+    // per-slot and per-bin passes walk the list with fixed grids
+    const bool wl = V.n_rep > 1 && !all;
+    KArgs as = a;
+    as.wl = wl ? 1 : 0;
+    const dim3 gs(wl ? (unsigned)(V.n_sm * 8) : (unsigned)((V.n_pad + 255) / 256));
+    if (wl) seq.push_back(KCall{(const void *)k_worklist, dim3(1), dim3(1024), 0, a});
     seq.push_back(KCall{(const void *)k_zero_bins, dim3(V.n_rep), dim3(256), 0, a});
-    KArgs ap = a;
+    KArgs ap = as;
     ap.mode = staged ? 1 : 0;
-    seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_prepare<MD_PREC_FP64>
-                                               : (const void *)k_prepare<MD_PREC_MIXED>,
-                        dim3(nb), dim3(256), 0, ap});
+    seq.push_back(KCall{fp64 ? (const void *)k_prepare<MD_PREC_FP64> : (const void *)k_prepare<MD_PREC_MIXED>, gs,
+                        dim3(256), 0, ap});
     const int nblk = (V.nbins_total + kScanBlock - 1) / kScanBlock;
     seq.push_back(KCall{(const void *)k_scan1, dim3(nblk), dim3(1024), 0, a});
     seq.push_back(KCall{(const void *)k_scan2, dim3(1), dim3(1024), 0, a});
     seq.push_back(KCall{(const void *)k_scan3, dim3((V.nbins_total + 255) / 256), dim3(256), 0, a});
-    seq.push_back(KCall{(const void *)k_scatter, dim3(nb), dim3(256), 0, a});
-    seq.push_back(KCall{V.prec == MD_PREC_FP64 ? (const void *)k_gather<MD_PREC_FP64>
-                                               : (const void *)k_gather<MD_PREC_MIXED>,
-                        dim3(nb), dim3(256), 0, a});
+    seq.push_back(KCall{(const void *)k_scatter, gs, dim3(256), 0, as});
+    seq.push_back(KCall{fp64 ? (const void *)k_gather<MD_PREC_FP64> : (const void *)k_gather<MD_PREC_MIXED>, gs,
+                        dim3(256), 0, as});
     if (V.tile_atoms > 0)
         seq.push_back(KCall{(const void *)k_tiles, dim3((V.n_ftiles + 3) / 4), dim3(128), 0, a});
-    const bool fp64 = V.prec == MD_PREC_FP64;
-    if (V.n_rep > 1 && !all) {
-        // a batch rebuilding some of its replicas: list their bins, fixed grid
+    if (wl) {
         const void *kb = fp64 ? (V.half ? (const void *)k_build_wl<MD_PREC_FP64, 1> : (const void *)k_build_wl<MD_PREC_FP64, 0>)
                               : (V.half ? (const void *)k_build_wl<MD_PREC_MIXED, 1> : (const void *)k_build_wl<MD_PREC_MIXED, 0>);
-        seq.push_back(KCall{(const void *)k_worklist, dim3(1), dim3(1024), 0, a});
         seq.push_back(KCall{kb, dim3(V.n_sm * (32 / kBuildWarps)), dim3(32 * kBuildWarps), 0, a});
         return;
     }

@@ -557,6 +557,8 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(h->d_ctl, 1);
     AL(V.wl_u0, (size_t)n_rep + 1);
     AL(V.wl_bin, (size_t)n_rep);
+    AL(V.wl_s0, (size_t)n_rep + 1);
+    AL(V.wl_a0, (size_t)n_rep);
     AL(V.wl_n, 1);
     {
         int dev = 0, nsm = 0;

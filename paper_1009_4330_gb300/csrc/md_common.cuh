@@ -130,8 +130,9 @@ struct View {
     uint32_t *nlist;
     int *ncount;
     // batched rebuild work list (k_worklist): per flagged replica, its first
-    // (bin, part) unit in a flat numbering [n_flagged + 1] and its first bin
-    int *wl_u0, *wl_bin, *wl_n;
+    // (bin, part) unit and its first slot in flat numberings [n_flagged + 1],
+    // its first bin and its first slot
+    int *wl_u0, *wl_bin, *wl_s0, *wl_a0, *wl_n;
     int n_sm;             // SMs of the device (fixed grids)
     // EAM
     double *fp64;         // F'(rho) per atom (fp64 path)
@@ -164,6 +165,7 @@ struct KArgs {
     int all;        // rebuild: 1 = every replica, 0 = replicas flagged by the drift
     int in_graph;   // 1: the kernel may set graph conditionals
     int aux;
+    int wl;         // rebuild kernels: walk the work list of flagged replicas (batches)
 };
 
 // force-kernel epilogue modes
