@@ -120,21 +120,21 @@ __device__ __forceinline__ int wl_slot(const View &V, int nf, int u) {
 }
 
 // the slots of one rebuild pass: every slot, or (a.wl) the work list's
-#define FOR_REBUILD_SLOTS(p, body)                                                                  \
-    if (a.wl) {                                                                                     \
-        const int nf_ = *V.wl_n, total_ = V.wl_s0[nf_];                                             \
-        for (int u_ = blockIdx.x * blockDim.x + threadIdx.x; u_ < total_; u_ += gridDim.x * blockDim.x) { \
-            const int p = wl_slot(V, nf_, u_);                                                      \
-            body;                                                                                   \
-        }                                                                                           \
-    } else {                                                                                        \
-        const int p = blockIdx.x * blockDim.x + threadIdx.x;                                        \
-        if (p < V.n_pad) { body; }                                                                  \
+template <class F>
+__device__ __forceinline__ void for_rebuild_slots(const View &V, const KArgs &a, F &&slot) {
+    if (a.wl) {
+        const int nf = *V.wl_n, total = V.wl_s0[nf];
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x)
+            slot(wl_slot(V, nf, u));
+    } else {
+        const int p = blockIdx.x * blockDim.x + threadIdx.x;
+        if (p < V.n_pad) slot(p);
     }
+}
 
 template <int PREC>
 __global__ void k_prepare(View V, KArgs a) {
-    FOR_REBUILD_SLOTS(p, prepare_slot<PREC>(V, a, p))
+    for_rebuild_slots(V, a, [&](int p) { prepare_slot<PREC>(V, a, p); });
 }
 
 // Bins of a replica are numbered along a Morton (Z-order) curve through its
@@ -232,7 +232,7 @@ __device__ __forceinline__ void scatter_slot(const View &V, const KArgs &a, int 
 }
 
 __global__ void k_scatter(View V, KArgs a) {
-    FOR_REBUILD_SLOTS(p, scatter_slot(V, a, p))
+    for_rebuild_slots(V, a, [&](int p) { scatter_slot(V, a, p); });
 }
 
 // Final slot = bin start + rank of the atom's id inside its bin (so the
@@ -285,7 +285,7 @@ __device__ __forceinline__ void gather_slot(const View &V, const KArgs &a, int q
 
 template <int PREC>
 __global__ void k_gather(View V, KArgs a) {
-    FOR_REBUILD_SLOTS(q, gather_slot<PREC>(V, a, q))
+    for_rebuild_slots(V, a, [&](int q) { gather_slot<PREC>(V, a, q); });
 }
 
 // global bin of slot p (after the gather)
