@@ -502,8 +502,8 @@ constexpr int kBatch = 14;  // rounds whose list entries are appended together
 constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
 
 template <int PREC, int HALF>
-__device__ __forceinline__ void build_cell(const View &V, int gb, int part, int lane, int w, int &my_max,
-                                           long long &my_sum) {
+__device__ __forceinline__ void build_cell(const View &V, int gb, int part, int hsplit, int lane, int w,
+                                           int &my_max, long long &my_sum) {
     __shared__ float4 s_h[kBuildWarps][32];
     __shared__ float4 s_q[kBuildWarps][kQueue];  // shifted candidate position, .w = list entry bits
     __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
@@ -534,7 +534,7 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
     const float rl2f = 0.5f * (V.rl2f_lo + V.rl2f_hi), margin = 0.5f * (V.rl2f_hi - V.rl2f_lo);
     // box pre-test bound: above every squared distance the margin band can hold
     const float keep2 = V.rl2f_hi + margin;
-    for (int h0 = 32 * part; h0 < hn; h0 += 32 * V.hsplit) {
+    for (int h0 = 32 * part; h0 < hn; h0 += 32 * hsplit) {
         const int nh = min(32, hn - h0);
         const int hbase = hs + h0;  // slot of home atom 0 of this chunk
         __syncwarp();
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
     if (gb < V.nbins_total) {
         const int r = V.bin_rep[gb];
         my_rep = r;
-        if (a.all || V.rep_flag[r]) build_cell<PREC, HALF>(V, gb, part, lane, w, my_max, my_sum);
+        if (a.all || V.rep_flag[r]) build_cell<PREC, HALF>(V, gb, part, V.hsplit, lane, w, my_max, my_sum);
     }
     // statistics per replica: warp max / sum, merged over the block's warps
     // that belong to the same replica, one atomic per run
@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
     for (int q0 = 0; q0 < V.n_rep; q0 += blockDim.x) {
         const int q = q0 + threadIdx.x;
         const bool f = q < V.n_rep && (a.all || V.rep_flag[q]);
-        const int units = f ? V.rep[q].nbins * V.hsplit : 0;
+        const int units = f ? V.rep[q].nbins * V.rep[q].hsplit : 0;
         const int slots = f ? V.rep[q].ntiles * 32 : 0;
         int tot_u, tot_s, tot_n;
         const int eu = block_excl_scan(units, s_warp, &tot_u);
@@ -839,6 +839,7 @@ __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
         if (f) {
             V.wl_u0[base_n + en] = base_u + eu;
             V.wl_bin[base_n + en] = V.rep[q].bin0;
+            V.wl_hs[base_n + en] = V.rep[q].hsplit;
             V.wl_s0[base_n + en] = base_s + es;
             V.wl_a0[base_n + en] = V.rep[q].atom0;
         }
@@ -869,10 +870,11 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build_wl
             else hi = mid - 1;
         }
         const int local = u - __ldg(&V.wl_u0[lo]);
-        const int gb = __ldg(&V.wl_bin[lo]) + local / V.hsplit, part = local % V.hsplit;
+        const int hs = __ldg(&V.wl_hs[lo]);
+        const int gb = __ldg(&V.wl_bin[lo]) + local / hs, part = local % hs;
         int my_max = 0;
         long long my_sum = 0;
-        build_cell<PREC, HALF>(V, gb, part, lane, w, my_max, my_sum);
+        build_cell<PREC, HALF>(V, gb, part, hs, lane, w, my_max, my_sum);
         for (int o = 16; o > 0; o >>= 1) {
             my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
             my_sum += __shfl_xor_sync(0xffffffffu, my_sum, o);

@@ -449,9 +449,14 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     V.nbins_total = bin0;
     {
         // enough warps per cell that a cell's home chunks of 32 atoms run side by side
+        auto split = [](double mean) { return std::max(1, std::min(8, (int)std::ceil(1.15 * mean / 32.0))); };
         double mean = 0.0;
-        for (const Rep &R : h->reps) mean = std::max(mean, (double)R.natoms / (double)R.nbins);
-        V.hsplit = std::max(1, std::min(8, (int)std::ceil(1.15 * mean / 32.0)));
+        for (Rep &R : h->reps) {
+            const double m = (double)R.natoms / (double)R.nbins;
+            R.hsplit = split(m);  // a replica's own cells (work-list builds of a batch)
+            mean = std::max(mean, m);
+        }
+        V.hsplit = split(mean);
     }
     V.prec = h->cfg.prec;
     V.pot = h->cfg.pot;
@@ -557,6 +562,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(h->d_ctl, 1);
     AL(V.wl_u0, (size_t)n_rep + 1);
     AL(V.wl_bin, (size_t)n_rep);
+    AL(V.wl_hs, (size_t)n_rep);
     AL(V.wl_s0, (size_t)n_rep + 1);
     AL(V.wl_a0, (size_t)n_rep);
     AL(V.wl_n, 1);

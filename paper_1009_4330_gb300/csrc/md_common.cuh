@@ -61,6 +61,7 @@ struct Rep {                // one replica (periodic box), device-resident
     int bin0, nbins;        // first global bin, number of bins
     int atom0, natoms;      // first slot, real atoms
     int tile0, ntiles;      // first 32-atom tile, tiles
+    int hsplit;             // warps sharing each of its cells in a work-list build
     long long orig0;        // offset of this replica in the caller's concatenated arrays
 };
 
@@ -131,8 +132,8 @@ struct View {
     int *ncount;
     // batched rebuild work list (k_worklist): per flagged replica, its first
     // (bin, part) unit and its first slot in flat numberings [n_flagged + 1],
-    // its first bin and its first slot
-    int *wl_u0, *wl_bin, *wl_s0, *wl_a0, *wl_n;
+    // its first bin, its warps per cell and its first slot
+    int *wl_u0, *wl_bin, *wl_hs, *wl_s0, *wl_a0, *wl_n;
     int n_sm;             // SMs of the device (fixed grids)
     // EAM
     double *fp64;         // F'(rho) per atom (fp64 path)
