@@ -275,6 +275,44 @@ def test_batch_trajectory_matches_oracle(batch_case):
         o += n
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_partial_batch_rebuild_gives_exact_lists(batch_case, prec):
+    """Step a batch until a step rebuilds some replicas but not all (the
+    work-list build and sort passes): every replica rebuilt in that step has
+    exactly the oracle's Verlet sets at the current positions, and every list is
+    still valid (all pairs within rc present, none beyond rc + 2 skin)."""
+    from paper_1009_4330_gb300 import System, lj_params
+    n_rep = len(batch_case)
+    with System.batch(batch_case, params=lj_params(1.0, 1.0, 1), cutoff=RC, skin=SKIN, dt=DT, mass=1.0,
+                      precision=prec, tpa=1) as s:
+        for _ in range(400):
+            before = s.info()["rebuilds"]
+            s.step(1)
+            k = s.info()["rebuilds"] - before
+            if 0 < k < n_rep:
+                break
+        else:
+            pytest.fail("no step rebuilt a strict subset of the replicas")
+        x = s.state()[0].cpu().numpy()
+        counts, nbr = s.neighbors()
+        lists = gpu_lists(counts, nbr)
+    o = 0
+    exact = 0
+    for rep in batch_case:
+        n = rep["x"].shape[0]
+        xr, box = x[o:o + n], rep["box"]
+        got = lists[o:o + n]
+        ref = oracle.neighbors(xr, box, RC + SKIN)
+        if margin_ok(xr, box, RC + SKIN) and all(np.array_equal(g, r) for g, r in zip(got, ref)):
+            exact += 1
+        inner = oracle.neighbors(xr, box, RC)
+        outer = oracle.neighbors(xr, box, RC + 2 * SKIN)
+        for i in range(n):
+            assert set(inner[i].tolist()) <= set(got[i].tolist()) <= set(outer[i].tolist())
+        o += n
+    assert exact >= k
+
+
 # --------------------------------------------------------------- errors ----
 
 def test_list_overflow_grows_capacity():
