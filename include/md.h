@@ -227,8 +227,9 @@ md_status md_cell_forces(md_system *h, double *f_out, int32_t reps, double *ms_o
 
 /*
  * md_step without CUDA graphs: the step's kernels are launched one by one
- * and the list-rebuild kernels every step (each returns at once for replicas
- * whose displacement check did not ask for a rebuild).  Same results as
+ * and the list-rebuild kernels every step (they do no work for replicas whose
+ * displacement check did not ask for a rebuild; a batch's rebuild kernels
+ * walk a list of the replicas that did).  Same results as
  * md_step; slower per step.  For profilers that cannot follow kernels inside
  * conditional graph nodes, and for environments without them.  An overflow
  * of the list capacity is reported (MD_ERR_LIST_OVERFLOW), not recovered.
