@@ -934,8 +934,8 @@ __device__ __forceinline__ float drift_pair(const View &V, int p, int first, int
         x[c] = *(const double2 *)&V.xr[c * n + p];
         v[c] = *(const double2 *)&V.v[c * n + p];
     }
-    const int2 t = *(const int2 *)&V.type[p];
     const float4 b0 = V.recb[p], b1 = V.recb[p + 1];
+    const int2 t = make_int2(__float_as_int(b0.w), __float_as_int(b1.w));  // the build records hold the types
     if (first) {
         const double hk0 = 0.5 * V.dt * V.tab->ftm_m[t.x], hk1 = two ? 0.5 * V.dt * V.tab->ftm_m[t.y] : 0.0;
         for (int c = 0; c < 3; ++c) {
