@@ -92,7 +92,9 @@ def barrier(dist):
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running,
+    each sample stamped with the host clock so that the samples inside a
+    region (the timed steps) can be told from the rest of the window."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -106,7 +108,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -116,7 +118,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            self.rows.append([time.time()] + [c.strip() for c in line.split(",")])
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -126,20 +128,36 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+    @staticmethod
+    def _summ(rows):
+        # row: [host time, index, sm, max sm, power, active, hw, hw_thermal, sw_thermal, sw_power_cap]
+        rows = [r[1:] for r in rows if len(r) > 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
-            if len(r) > 8:
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower().startswith("active"):
-                        reasons.add(nm)
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+    def summary(self, t0=None, t1=None, window=""):
+        """Clocks of the samples between host times t0 and t1 (the timed
+        region); if that region was shorter than the sampling period, those of
+        the whole window, which brackets it with the same kernels running."""
+        inside = self._summ([r for r in self.rows if t0 is not None and t0 <= r[0] <= t1])
+        whole = self._summ(self.rows)
+        if inside is not None:
+            inside["region"] = "timed steps"
+            return inside
+        if whole is not None:
+            whole["region"] = window or "sampling window"
+            return whole
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
 
 
 # ------------------------------------------------------------- workloads --
@@ -157,7 +175,10 @@ def info0_is_full(s):
     return s.info()["list"] == "full"
 
 
-def time_steps(s, K, W, sampler_gpu=None, eager=False, before=None):
+def time_steps(s, K, W, eager=False, before=None, region=None):
+    """W untimed steps, then K steps timed with CUDA events on the handle's
+    stream (torch's current stream), synchronised on both sides.  region: a
+    list that receives the host times bracketing the timed steps."""
     import torch
     s.step(W, eager=eager)
     torch.cuda.synchronize()
@@ -166,19 +187,18 @@ def time_steps(s, K, W, sampler_gpu=None, eager=False, before=None):
     i0 = s.info()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(sampler_gpu) if sampler_gpu is not None else None
-    if clocks:
-        clocks.__enter__()
     torch.cuda.synchronize()
+    t0 = time.time()
     e0.record()
     s.step(K, eager=eager)
     e1.record()
     torch.cuda.synchronize()
-    if clocks:
-        clocks.__exit__()
+    t1 = time.time()
+    if region is not None:
+        region[:] = [t0, t1]
     i1 = s.info()
     ms = e0.elapsed_time(e1)
-    return ms, i0, i1, (clocks.summary() if clocks else None)
+    return ms, i0, i1, None
 
 
 def total_energy(s):
@@ -186,22 +206,46 @@ def total_energy(s):
     return float(ev[0] + ev[1])
 
 
-def accuracy_report(s, d, e_start, K):
-    """Mixed precision against the plain FP64 GPU path (which the tests hold to
-    the FP64 oracle at 1e-12): the force error at the state after the timed
-    steps, and the NVE drift of the shifted total energy over those steps."""
+DRIFT_STEPS, DRIFT_EVERY = 1000, 50
+
+
+def nve_drift(s, n, steps=DRIFT_STEPS, every=DRIFT_EVERY):
+    """NVE energy conservation of a running system: E_tot/N (shifted energy)
+    sampled every `every` steps over `steps` steps; the least-squares slope x
+    1000 (drift per atom per 1,000 steps) and the largest excursion
+    max |E(t) - E(0)| / N.  Independent of the bench's --steps."""
+    es = []
+    for k in range(steps // every + 1):
+        es.append(total_energy(s) / n)
+        if k < steps // every:
+            s.step(every)
+    t = np.arange(len(es)) * every
+    slope = float(np.polyfit(t, np.array(es), 1)[0])
+    return {"drift_per_atom_per_1000_steps": slope * 1000.0, "max_excursion_per_atom": float(np.abs(np.array(es) - es[0]).max()),
+            "steps": steps, "sampled_every": every, "e_per_atom_start": es[0]}
+
+
+def accuracy_report(s, d):
+    """Accuracy stated with the throughput, on the bench workload itself:
+    (1) mixed-precision forces against the plain FP64 GPU path (which the
+    tests hold to the FP64 oracle at 1e-12) at the state after the timed
+    steps; (2) NVE drift over 1,000 further steps of the mixed run, and over
+    1,000 steps of the plain FP64 path from the same state (least-squares
+    slope of the shifted total energy per atom, x 1000)."""
     from paper_1009_4330_gb300 import System
     n = d["x"].shape[0]
-    drift = (total_energy(s) - e_start) / n * (1000.0 / K)
     x, v, _ = s.state()
     f_mixed = s.compute_forces().cpu().numpy()
     with System.lj(x, v, d["box"], cutoff=d["rc"], skin=d["skin"], dt=d["dt"], mass=1.0, precision="fp64",
-                   list="full", tpa=4) as s64:
+                   list="full", tpa=4, energy_shift=True) as s64:
         f64 = s64.compute_forces().cpu().numpy()
-    err = float(np.abs(f_mixed - f64).max() / np.abs(f64).max())
+        err = float(np.abs(f_mixed - f64).max() / np.abs(f64).max())
+        drift64 = nve_drift(s64, n)
+    drift_mixed = nve_drift(s, n)
     return {"mixed_force_rel_maxnorm_vs_fp64": err, "force_tolerance": 1e-5,
-            "nve_drift_per_atom_per_1000_steps": drift, "drift_bound": 1e-4,
-            "energy": "shifted LJ (continuous at rc)", "state": f"after the {K} timed steps"}
+            "nve_drift_mixed": drift_mixed, "nve_drift_fp64": drift64, "drift_bound": 1e-4,
+            "drift_definition": "least-squares slope of E_tot/N vs step, x 1000",
+            "energy": "shifted LJ (continuous at rc)", "state": "from the state after the timed steps"}
 
 
 def e2e_run(s, d, K):
@@ -293,14 +337,24 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-# DRAM traffic of the force kernel per atom, from the ncu capture summarised in
-# profiles/k_lj_lj500k_mixed_full.md (the md_step form of the pass:
-# dram__bytes_read.sum + dram__bytes_write.sum = 182.09 + 4.45 MB for 500,000
-# atoms; scaled by atoms, the list length per atom being the same).  Valid for
-# that variant only: T = 1 thread per atom, Q = 4, full list, 128-thread blocks,
-# records gathered (no staging).
+# DRAM bytes per atom that one launch of the force kernel moves
+# (dram__bytes_read.sum + dram__bytes_write.sum), from one ncu capture of a
+# 500,000-atom case of this workload, scaled by atoms (the list length per
+# atom is the same).  Valid only for this kernel variant, as captured; for
+# any other variant roofline.traffic is null.
 K_LJ_TRAFFIC_PER_ATOM = (182.090752e6 + 4.451840e6) / 500000
 K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full", "block": 128, "tile_atoms": 0}
+
+# FP32 operations per list entry of the mixed full-list pair loop (a fused
+# multiply-add counted as 2), counted from its source: the separation with
+# the stencil offset 3 + 6 + 3 (offset decode), r^2 5, reciprocal 1, r^-6 2,
+# the pair coefficient 4, the cut-off test and band minimum 2, the three
+# force sums 6, the compensated round sums 3 (12 additions per 4 entries).
+FP32_OPS_PER_ENTRY = 35
+# FP64 operations per list entry of the FP64 pair loop, counted the same way:
+# separation 9, r^2 5, Newton reciprocal 7, r^-6 2, coefficient 4, cut-off 1,
+# force sums 6.
+FP64_OPS_PER_ENTRY = 34
 
 
 def load_peaks():
@@ -313,24 +367,60 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def roofline_of(f_ms, f_bytes, entries, g_ms, ceil, peak, peak_kind, traffic):
+    """The force pass against the three ceilings: HBM (its algorithmic bytes
+    per launch), random 16-byte gathers from L2 (its list entries, one record
+    gather each), the FP32 pipe (its pair-loop operations), plus its own
+    access pattern's ceiling (the memory-only twin)."""
+    sec = f_ms / 1000.0
+    achieved = f_bytes / sec / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic,
+           "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 500,000-atom capture of this "
+                             "kernel variant, scaled by atoms" if traffic else None,
+           "kernel": "k_lj (force + kick, md_step form)", "peak_kind": peak_kind,
+           "force_ms": f_ms, "force_algorithmic_bytes": f_bytes}
+    ceilings = {"hbm": {"peak_GBs": peak, "achieved_GBs": achieved, "frac": achieved / peak, "source": peak_kind}}
+    if ceil:
+        gps = entries / sec / 1e9
+        ceilings["l2_gather"] = {"peak_Ggathers_s": ceil["l2_gather_gps"], "achieved_Ggathers_s": gps,
+                                 "frac": gps / ceil["l2_gather_gps"], "source": "md_probe_ceilings"}
+        tf = FP32_OPS_PER_ENTRY * entries / sec / 1e12
+        ceilings["fp32"] = {"peak_TFLOPs": ceil["fp32_fma_tflops"], "achieved_TFLOPs": tf,
+                            "frac": tf / ceil["fp32_fma_tflops"], "ops_per_entry": FP32_OPS_PER_ENTRY,
+                            "source": "md_probe_ceilings"}
+        ceilings["hbm_own_copy_GBs"] = ceil["hbm_copy_gbs"]
+    if g_ms:
+        ceilings["access_pattern_twin"] = {"twin_ms": g_ms, "frac": g_ms / f_ms,
+                                           "note": "the same list stream and record gathers, no arithmetic"}
+    out["ceilings"] = ceilings
+    fr = {k: v["frac"] for k, v in ceilings.items() if isinstance(v, dict) and "frac" in v}
+    out["binding"] = max(fr, key=fr.get) if fr else "hbm"
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import synth
+    from paper_1009_4330_gb300 import probe_ceilings
     torch.cuda.set_device(local)
     dist = dist_init(ws)
     cells = args.cells
+    # clocks sampled from before the warm-up to the end of the accuracy legs
+    # (same kernels throughout); the timed steps' own samples are preferred
+    clocks = ClockSampler(local)
+    clocks.__enter__()
     # tpa 0: the set-up mini-benchmark picks threads per atom, list kind and block size
     s, d = make_lj(synth, cells, 2.5, "mixed", tpa=args.tpa, lst=args.list if args.tpa else "auto")
+    tune = s.autotune_table()
     if args.tpa and args.vec:
         s.set_kernel(args.tpa, args.list if args.list != "auto" else "full", args.block, args.vec)
     n = d["x"].shape[0]
     K, W = args.steps, max(3, args.warmup)
     barrier(dist)
-    e_start = []
-    ms, i0, i1, clocks = time_steps(s, K, W, sampler_gpu=local, eager=args.eager,
-                                    before=lambda: e_start.append(total_energy(s)))
+    region = []
+    ms, i0, i1, _ = time_steps(s, K, W, eager=args.eager, region=region)
     ms = max_over_ranks(dist, ms)
-    accuracy = accuracy_report(s, d, e_start[0], K) if rank == 0 else None
     value = ws * n * K / (ms / 1000.0)
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
     # our kernels in the timed region: loop control once, per step the drift and
@@ -338,17 +428,24 @@ def run_ours(args, ws, rank, local):
     launches = 1 + K * (1 + (3 if i1["list"] == "half" else 1)) + (9 if i1["tile_atoms"] else 8) * rebuilds
     # dominant kernel: the force pass as md_step runs it, timed with CUDA events on the handle's stream
     f_ms, f_bytes = s.time_force(warmup=3, reps=20)
-    # the ceiling of the same access pattern: the force pass's memory-only twin
-    g_ms = s.time_gather(warmup=3, reps=20) if info0_is_full(s) else None
-    peak, peak_kind = load_peaks()
-    achieved = f_bytes / (f_ms / 1000.0) / 1e9
     info = s.info()
+    # the ceiling of the same access pattern: the force pass's memory-only twin
+    g_ms = s.time_gather(warmup=3, reps=20) if info["list"] == "full" else None
+    accuracy = accuracy_report(s, d) if rank == 0 else None
+    clocks.__exit__()
+    clk = clocks.summary(region[0], region[1],
+                         window="set-up, warm-up, timed steps, force timings and the 1,000-step accuracy runs "
+                                "(the timed steps alone were shorter than the 100 ms sampling period)")
+    peak, peak_kind = load_peaks()
+    ceil = probe_ceilings() if rank == 0 else None
     same_variant = all(info[k] == v for k, v in K_LJ_TRAFFIC_VARIANT.items())
     traffic = K_LJ_TRAFFIC_PER_ATOM * n if same_variant else None
+    roof = roofline_of(f_ms, f_bytes, info["list_entries"], g_ms, ceil, peak, peak_kind, traffic)
+    roof["force_share_of_step"] = f_ms / (ms / K)
     e2e = e2e_run(s, d, K)
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = side_runs(synth, cells, K, W)
+        extras = side_runs(synth, cells, K, W, ceil, tune_rc25=tune)
     cpu = cpu_baseline(synth, cells, args.cpu_seconds) if (rank == 0 and ws == 1) else None
     s.close()
     if rank == 0:
@@ -362,17 +459,12 @@ def run_ours(args, ws, rank, local):
                        "avg_list_length": info["list_entries"] / n, "rebuilds_in_timed_region": rebuilds,
                        "steps_per_rebuild": (K / rebuilds) if rebuilds else None,
                        "l2": "working set > L2 (list alone ~0.3 GB): no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "traffic_source": "profiles/k_lj_lj500k_mixed_full.md (scaled by atoms)",
-                         "kernel": "k_lj (force + kick, md_step form)", "peak_kind": peak_kind,
-                         "force_ms": f_ms, "force_algorithmic_bytes": f_bytes,
-                         "access_pattern_ceiling": ({"memory_only_twin_ms": g_ms, "achieved_GBs": f_bytes / (g_ms / 1000.0) / 1e9,
-                                                     "frac": g_ms / f_ms} if g_ms else None),
-                         "force_share_of_step": f_ms / (ms / K)},
-            "clocks": clocks,
+            "roofline": roof,
+            "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,
             "accuracy": accuracy,
+            "autotune": tune,
             "cpu_baseline": cpu,
             "extras": extras,
         }
@@ -381,22 +473,118 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def side_runs(synth, cells, K, W):
-    """Context numbers: plain FP64 on the same workload, rc 5.0, EAM, batched replicas."""
+def step_arm(s, n, k, W):
+    """md_step throughput of a system as configured, CUDA events."""
+    ms, i0, i1, _ = time_steps(s, k, W)
+    inf = s.info()
+    return {"value": n * k / (ms / 1000), "ms_per_step": ms / k, "steps": k, "tpa": inf["tpa"], "list": inf["list"],
+            "vec": inf["vec"], "block": inf["block"], "rebuilds": i1["rebuilds"] - i0["rebuilds"]}
+
+
+def force_arm(s, ceil, prec):
+    """The force pass alone (md_step form), with its pipe fraction for the precision's pipe."""
+    fms, fby = s.time_force(3, 10)
+    inf = s.info()
+    out = {"force_ms": fms, "force_GBs": fby / (fms / 1000) / 1e9}
+    if ceil and s.potential == "lj" and inf["list"] == "full":
+        if prec == "fp64":
+            tf = FP64_OPS_PER_ENTRY * inf["list_entries"] / (fms / 1000) / 1e12
+            out["fp64_TFLOPs"] = tf
+            out["fp64_pipe_frac"] = tf / ceil["fp64_fma_tflops"]
+        else:
+            tf = FP32_OPS_PER_ENTRY * inf["list_entries"] / (fms / 1000) / 1e12
+            out["fp32_TFLOPs"] = tf
+            out["fp32_pipe_frac"] = tf / ceil["fp32_fma_tflops"]
+    return out
+
+
+def best_of(tune, lst):
+    rows = [r for r in tune if r["list"] == lst]
+    return min(rows, key=lambda r: r["ms"]) if rows else None
+
+
+def lj_pair(synth, cells, rc, K, W, ceil, tune=None):
+    """LJ liquid at cut-off rc: mixed (autotuned) with its best full-list and
+    best half-list variants' step times, and the plain FP64 path (autotuned)."""
+    out = {}
+    k = max(50, K // 4) if rc > 3 else max(50, K // 5)
+    s, d = make_lj(synth, cells, rc, "mixed", tpa=0)
+    n = d["x"].shape[0]
+    tune = tune if tune is not None else s.autotune_table()
+    m = step_arm(s, n, k, W)
+    m.update(force_arm(s, ceil, "mixed"))
+    out["mixed"] = m
+    for lst in ("full", "half"):
+        b = best_of(tune, lst)
+        if b is None:
+            continue
+        s.set_kernel(b["tpa"], lst, b["block"], b["vec"])
+        a = step_arm(s, n, k, W)
+        a["force_ms_autotune"] = b["ms"]
+        out[f"mixed_{lst}_list"] = a
+    out["autotune"] = tune
+    s.close()
+    s, _ = make_lj(synth, cells, rc, "fp64", tpa=0)
+    k64 = max(20, k // 10)
+    f = step_arm(s, n, k64, 3)
+    f.update(force_arm(s, ceil, "fp64"))
+    out["fp64"] = f
+    out["fp64_autotune"] = s.autotune_table()
+    s.close()
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def side_runs(synth, cells, K, W, ceil, tune_rc25=None):
+    """Context numbers: every workload in mixed precision and in plain FP64
+    (same inputs), half against full lists, the design alternatives, the CPU
+    cell-list baseline, the backward passes."""
     import torch
     from paper_1009_4330_gb300 import System, lj_params
     out = {}
-    # plain FP64 GPU path, same workload
-    s, d = make_lj(synth, cells, 2.5, "fp64", tpa=0)
-    k = max(20, K // 10)
-    ms, i0, i1, _ = time_steps(s, k, 3)
-    n = d["x"].shape[0]
-    out["fp64_rc2.5"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"]}
+    out["ceilings"] = ceil
+    out["lj864k_rc2.5"] = lj_pair(synth, cells, 2.5, K, W, ceil)
+    out["lj864k_rc5.0"] = lj_pair(synth, cells, 5.0, K, W, ceil)
+    # EAM 500,000 atoms (full lists only)
+    e = synth.config2()
+    ne = e["x"].shape[0]
+    eam = {}
+    for prec in ("mixed", "fp64"):
+        s = System.eam(e["x"], e["v"], e["box"], eam_params=e["eam"], skin=e["skin"], dt=e["dt"], mass=e["mass"],
+                       ftm2v=e["ftm2v"], precision=prec, tpa=0)
+        k = max(50, K // 2) if prec == "mixed" else max(20, K // 20)
+        a = step_arm(s, ne, k, 5)
+        a.update(force_arm(s, ceil, prec))
+        a["autotune"] = s.autotune_table()
+        eam[prec] = a
+        s.close()
+    eam["mixed_over_fp64"] = eam["mixed"]["value"] / eam["fp64"]["value"]
+    out["eam500000"] = eam
+    # batched replicas (512, log-uniform 500..20000)
+    b = synth.config4()
+    nb = int(sum(b["sizes"]))
+    bat = {}
+    for prec in ("mixed", "fp64"):
+        s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
+                         precision=prec, tpa=0)
+        k = max(50, K // 4) if prec == "mixed" else max(20, K // 40)
+        a = step_arm(s, nb, k, 5)
+        a.update(force_arm(s, ceil, prec))
+        a["atoms"] = nb
+        bat[prec] = a
+        s.close()
+    bat["mixed_over_fp64"] = bat["mixed"]["value"] / bat["fp64"]["value"]
+    out["batch512"] = bat
+    # 4,000-atom LJ liquid, plain FP64, 100 steps (latency-bound small system)
+    c0 = synth.config0()
+    s = System.lj(c0["x"], c0["v"], c0["box"], cutoff=2.5, skin=0.3, dt=0.005, mass=1.0, precision="fp64", tpa=0)
+    ms, i0, i1, _ = time_steps(s, 100, 10)
+    out["fp64_lj4000_100steps"] = {"value": 4000 * 100 / (ms / 1000), "ms_per_step": ms / 100, "tpa": i1["tpa"],
+                                   "list": i1["list"]}
     s.close()
-    # O(N) CPU baseline: velocity Verlet with FP64 cell-list forces on the host
-    # cores, 2 steps of the same 864,000-atom liquid (the cpu_baseline of the
-    # line is the O(N^2) oracle)
-    out["cpu_celllist"] = cpu_celllist(synth, cells)
+    # force matching: forward forces + backward (positions and 6 parameters), 32,768 atoms
+    out["force_matching_32768"] = force_matching_timing(synth)
+    out["eam500000_fwd_bwd"] = eam_backward_timing(synth)
     # design alternative: block-local lists with shared-memory staging (off by
     # default), force pass and its memory-only twin against the default layout
     s, d = make_lj(synth, cells, 2.5, "mixed", tpa=1, lst="full")
@@ -414,45 +602,10 @@ def side_runs(synth, cells, K, W):
     alt["cell_list"] = {"force_ms": cms, "note": "27 cells tested per atom, no list read or built"}
     out["staging_alternative_rc2.5"] = alt
     s.close()
-    # rc 5.0, mixed
-    s, d = make_lj(synth, cells, 5.0, "mixed", tpa=0)
-    k = max(50, K // 4)
-    ms, i0, i1, _ = time_steps(s, k, 5)
-    fms, fby = s.time_force(3, 10)
-    out["mixed_rc5.0"] = {"value": n * k / (ms / 1000), "steps": k, "tpa": i1["tpa"], "list": i1["list"],
-                          "force_GBs": fby / (fms / 1000) / 1e9}
-    s.close()
-    # EAM 500,000 atoms, mixed
-    e = synth.config2()
-    s = System.eam(e["x"], e["v"], e["box"], eam_params=e["eam"], skin=e["skin"], dt=e["dt"], mass=e["mass"],
-                   ftm2v=e["ftm2v"], precision="mixed", tpa=0)
-    k = max(50, K // 2)
-    ms, i0, i1, _ = time_steps(s, k, 5)
-    fms, fby = s.time_force(3, 10)
-    out["eam500000_mixed"] = {"value": e["x"].shape[0] * k / (ms / 1000), "steps": k, "tpa": i1["tpa"],
-                              "force_GBs": fby / (fms / 1000) / 1e9}
-    s.close()
-    # 4,000-atom LJ liquid, plain FP64, 100 steps (latency-bound small system)
-    c0 = synth.config0()
-    s = System.lj(c0["x"], c0["v"], c0["box"], cutoff=2.5, skin=0.3, dt=0.005, mass=1.0, precision="fp64", tpa=0)
-    ms, i0, i1, _ = time_steps(s, 100, 10)
-    out["fp64_lj4000_100steps"] = {"value": 4000 * 100 / (ms / 1000), "ms_per_step": ms / 100, "tpa": i1["tpa"],
-                                   "list": i1["list"]}
-    s.close()
-    # force matching: forward forces + backward (positions and 6 parameters), 32,768 atoms
-    out["force_matching_32768"] = force_matching_timing(synth)
-    out["eam500000_fwd_bwd"] = eam_backward_timing(synth)
-    # batched replicas (512, log-uniform 500..20000), mixed
-    b = synth.config4()
-    s = System.batch(b["replicas"], params=lj_params(1.0, 1.0, 1), cutoff=2.5, skin=0.3, dt=0.005, mass=1.0,
-                     precision="mixed", tpa=0)
-    k = max(50, K // 4)
-    ms, i0, i1, _ = time_steps(s, k, 5)
-    nb = int(sum(b["sizes"]))
-    fms, fby = s.time_force(3, 10)
-    out["batch512_mixed"] = {"value": nb * k / (ms / 1000), "atoms": nb, "steps": k, "tpa": i1["tpa"],
-                             "force_GBs": fby / (fms / 1000) / 1e9}
-    s.close()
+    # O(N) CPU baseline: velocity Verlet with FP64 cell-list forces on the host
+    # cores, 2 steps of the same 864,000-atom liquid (the cpu_baseline of the
+    # line is the O(N^2) oracle)
+    out["cpu_celllist"] = cpu_celllist(synth, cells)
     torch.cuda.synchronize()
     return out
 

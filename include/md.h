@@ -29,8 +29,8 @@
  *     NULL = legacy default stream).  Entry points that must read a device
  *     value (md_create, md_step's list-overflow recovery, md_sync_status,
  *     md_autotune, md_info) synchronise that stream.  Errors found on the
- *     device (non-finite state, list overflow, wait time-outs) are latched in
- *     a device status word and returned by the next md_sync_status.
+ *     device (non-finite state, list overflow) are latched in a device
+ *     status word and returned by the next md_sync_status.
  *   - Errors: every entry point returns an md_status; md_last_error() gives
  *     a one-line message for the most recent failure on that handle (or the
  *     most recent handle-less failure when called with NULL).
@@ -61,7 +61,7 @@ typedef enum {
     MD_ERR_BOX_TOO_SMALL = 4,  /* a box edge < 2 (cutoff + skin)                        */
     MD_ERR_LIST_OVERFLOW = 5,  /* neighbour capacity exceeded and growing it failed     */
     MD_ERR_NONFINITE = 6,      /* a position, velocity or force became NaN/Inf          */
-    MD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                    */
+    MD_ERR_TIMEOUT = 7,        /* reserved: no kernel of this build waits on another    */
     MD_ERR_UNSUPPORTED = 8     /* valid request outside this build's limits             */
 } md_status;
 
@@ -111,11 +111,16 @@ md_status md_create(const md_config *cfg, const double *x, const double *v, cons
  * are host arrays of n_rep device pointers.  Every other entry point then
  * acts on all replicas at once; per-replica outputs are concatenated in
  * replica order.
+ * Cite: no paper passage defines batching -- the paper runs one system per
+ * GPU.  Each replica is advanced by the paper's method (Sec. II, Sec. III.B);
+ * many small systems share one launch so that the GPU gets the thousands of
+ * threads Sec. II (a) says it needs.
  */
 md_status md_batch_create(int32_t n_rep, const md_config *cfgs, const double *const *x,
                           const double *const *v, const int32_t *const *type, md_system **out);
 
-/* Release the handle and all its device memory (synchronises its stream). */
+/* Release the handle and all its device memory (synchronises its stream).
+ * Cite: no paper passage -- library plumbing. */
 md_status md_destroy(md_system *h);
 
 /*
@@ -130,12 +135,14 @@ md_status md_build_neighbors(md_system *h);
  * Evaluate forces at the current positions (pair forces over the list,
  * Sec. III.B listings) and store them; if f_out != NULL also write them to
  * f_out[n][3] in original order.
+ * Cite: Sec. III.B (the neighbour-list force kernels), App. A (lj/cut, EAM).
  */
 md_status md_compute_forces(md_system *h, double *f_out);
 
 /*
- * Advance nsteps velocity-Verlet NVE steps entirely on the device
- * (Sec. II: integration in double precision on the GPU).  Each step checks
+ * Advance nsteps velocity-Verlet NVE steps entirely on the device.
+ * Cite: Sec. II (the whole time step on the GPU, NVE integrator; in mixed
+ * precision the time integration stays in double precision).  Each step checks
  * the displacement criterion and rebuilds the list inside the same CUDA
  * graph when needed (no host round trip).  If a rebuild overflows the list
  * capacity, the library grows it and resumes from the interrupted step
@@ -148,16 +155,25 @@ md_status md_step(md_system *h, int64_t nsteps);
  * out[8*r + k] for replica r, k = {Epot, Ekin, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz}
  * with W_ab = sum over pairs of d_a f_b (d = x_i - x_j).  Device pointer,
  * 8 * n_rep doubles.  Summation order is fixed (deterministic).
+ * Cite: App. A (the potentials whose energies these are: lj/cut, EAM) and
+ * Sec. II (NVE dynamics, whose conserved total energy Epot + Ekin measures the
+ * integration error); the paper prints no formula, so these are the
+ * textbook definitions.
  */
 md_status md_energy_virial(md_system *h, double *out);
 
-/* Read the state in original order: x (wrapped into [0, L)), v, f -- any may be NULL. */
+/* Read the state in original order: x (wrapped into [0, L)), v, f -- any may be NULL.
+ * Cite: no paper passage -- library plumbing (the device-resident state of
+ * Sec. II, copied out). */
 md_status md_get_state(md_system *h, double *x, double *v, double *f);
 
-/* Replace positions and velocities (original order; either may be NULL), rebuild, recompute forces. */
+/* Replace positions and velocities (original order; either may be NULL), rebuild, recompute forces.
+ * Cite: no paper passage -- library plumbing. */
 md_status md_set_state(md_system *h, const double *x, const double *v);
 
-/* Replace the potential parameters (host, layout of md_config.params); takes effect for the next force. */
+/* Replace the potential parameters (host, layout of md_config.params); takes effect for the next force.
+ * Cite: App. A (the lj/cut and EAM parameters); changing them between force
+ * evaluations is library plumbing for force-matching loops. */
 md_status md_set_params(md_system *h, const double *params);
 
 /*
@@ -176,6 +192,9 @@ md_status md_set_params(md_system *h, const double *params);
  * nothing.  Pair terms and sums are in double precision in both modes.
  * grad_x or grad_params may be NULL.  Uses the current neighbour list, which
  * must be a full list (MD_ERR_UNSUPPORTED for a half list).
+ * Cite: no paper passage defines a backward pass; it differentiates the
+ * forces of Sec. III.B for the App. A potentials (chain rule, written out in
+ * the library's kernels), over the same neighbour list.
  */
 md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x, double *grad_params);
 
@@ -184,6 +203,8 @@ md_status md_forces_backward(md_system *h, const double *grad_f, double *grad_x,
  * (the paper's set-up mini-benchmark, Sec. III.B), then rebuild for the
  * winner.  cache_path (host string, may be NULL) names a text file of
  * earlier choices keyed by potential, precision, size and list length.
+ * Cite: Sec. III.B (both kernel variants kept and the faster one chosen by a
+ * built-in mini-benchmark during set-up).
  */
 md_status md_autotune(md_system *h, const char *cache_path);
 
@@ -193,6 +214,8 @@ md_status md_autotune(md_system *h, const char *cache_path);
  * {64,128,256}, vec (list entries per thread per load) in {1,2,4}.  Changing
  * tpa, list or vec rebuilds the list in the matching layout (and recomputes
  * the forces).
+ * Cite: Sec. III.B (thread-per-atom and block-per-atom force kernels, kept
+ * side by side and selected per system).
  */
 md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t block, int32_t vec);
 
@@ -208,6 +231,8 @@ md_status md_set_kernel(md_system *h, int32_t tpa, md_listkind list, int32_t blo
  * at the LJ-liquid densities the staged passes measured slower (shared-memory
  * bank conflicts of the scattered record reads, and the staging itself).
  * Rebuilds the lists when the layout changes.
+ * Cite: Sec. III.A (cell-based staging of neighbour data in shared memory),
+ * measured here as an alternative layout of the Sec. III.B list kernels.
  */
 md_status md_set_staging(md_system *h, int32_t on);
 
@@ -222,6 +247,8 @@ md_status md_set_staging(md_system *h, int32_t on);
  * runs a force pass (velocities read and written, zero kick; after 2 untimed
  * passes), ms_out (host) = ms per pass.  f_out (device [n][3], original
  * order, may be NULL): the forces from one pass.  The state is unchanged.
+ * Cite: Sec. III.A (the cell-list force approach), Sec. III.C (its
+ * comparison with neighbour lists).
  */
 md_status md_cell_forces(md_system *h, double *f_out, int32_t reps, double *ms_out);
 
@@ -233,6 +260,8 @@ md_status md_cell_forces(md_system *h, double *f_out, int32_t reps, double *ms_o
  * md_step; slower per step.  For profilers that cannot follow kernels inside
  * conditional graph nodes, and for environments without them.  An overflow
  * of the list capacity is reported (MD_ERR_LIST_OVERFLOW), not recovered.
+ * Cite: Sec. II (the same GPU time step as md_step, launched from the host
+ * kernel by kernel as the paper's implementation does).
  */
 md_status md_step_eager(md_system *h, int64_t nsteps);
 
@@ -262,7 +291,7 @@ typedef struct {
  * average milliseconds per force pass; bytes_out (host, may be NULL) the
  * algorithmic DRAM bytes of one pass: list entries actually present (4 B
  * each) plus, per atom, its record, list length and velocity in and out.
- * For measurement only; the paper has no counterpart.  Synchronises.
+ * Synchronises.  Cite: no paper passage -- measurement only.
  */
 md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_out, double *bytes_out);
 
@@ -273,15 +302,16 @@ md_status md_time_force(md_system *h, int32_t warmup, int32_t reps, double *ms_o
  * pair instead of the pair arithmetic -- the ceiling of the force pass's
  * access pattern on this GPU.  ms_out (host): average milliseconds per pass
  * over `reps` launches after `warmup`; state unchanged.  MD_ERR_UNSUPPORTED
- * for other potentials, precisions or list kinds.  For measurement only; the
- * paper has no counterpart.  Synchronises.
+ * for other potentials, precisions or list kinds.  Synchronises.
+ * Cite: no paper passage -- measurement only.
  */
 md_status md_time_gather(md_system *h, int32_t warmup, int32_t reps, double *ms_out);
 
-/* Statistics (synchronises). */
+/* Statistics (synchronises).  Cite: no paper passage -- library plumbing. */
 md_status md_info(md_system *h, md_info_t *out);
 
 /*
+ * Cite: Sec. III.B (numneigh[i], neighbors[i][jj]), copied out.
  * Copy the neighbour list out, for inspection and testing: counts[n] and
  * nbr[n][cap] (row-major; entries beyond counts[i] unspecified) in ORIGINAL
  * atom indices (within the replica for a batch).  Full list: every j with
@@ -292,11 +322,11 @@ md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t 
 
 /*
  * Neighbour lists without allocating anything -- for callers that may not
- * call cudaMalloc: work issued while a stream is being captured into a CUDA
- * graph, hosts whose device memory belongs entirely to another allocator (a
- * framework's caching pool, a fixed arena), latency-critical loops that
- * cannot afford an allocation.  The paper has no counterpart; this is a
- * library convenience beside the handle-based path.
+ * call cudaMalloc: hosts whose device memory belongs entirely to another
+ * allocator (a framework's caching pool, a fixed arena sized at start-up),
+ * and latency-critical loops that cannot afford an allocation and the
+ * device-wide synchronisation it may bring.  The paper has no counterpart;
+ * this is a library convenience beside the handle-based path.
  *
  * Builds the full Verlet neighbour sets of ONE periodic box: for every atom
  * i, all j != i with |x_i - x_j|^2 < rl^2 under the minimum image, decided
@@ -306,29 +336,79 @@ md_status md_get_neighbors(md_system *h, int32_t *counts, int32_t *nbr, int32_t 
  * int32[n][cap], row-major, original indices, unsorted within a row, only
  * the first min(count, cap) entries of a row written.  Work goes on
  * `stream` (a cudaStream_t; NULL = legacy default stream) and the call
- * synchronises it before returning.
+ * synchronises it before returning (it reads an overflow flag back), so it
+ * cannot be issued while that stream is being captured into a CUDA graph.
  *
  * Scratch: one static device array of about 2.6 MB per device that loads the
  * library, held until the process exits, limiting n to MD_NOALLOC_MAX_ATOMS
  * and the cell grid to MD_NOALLOC_MAX_BINS cells (coarser cells are used if
  * needed; results do not change).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress): make that first call before
- * any stream capture.  All calls share the array, so calls that overlap on
- * the GPU (other threads, other streams) race and must be serialised by the
- * caller.  Errors: MD_ERR_INVALID (null pointer, n, cap or rl not positive),
+ * array's device address (cudaGetSymbolAddress) and keeps it for that
+ * device; a device reset (cudaDeviceReset) afterwards is not supported.
+ * All calls share the array and each starts by clearing what it must
+ * (bin counts, the overflow flag), so calls that overlap on the GPU (other
+ * threads, other streams) race and must be serialised by the caller.  Errors: MD_ERR_INVALID (null pointer, n, cap or rl not positive),
  * MD_ERR_UNSUPPORTED (n > MD_NOALLOC_MAX_ATOMS), MD_ERR_BOX_TOO_SMALL,
  * MD_ERR_LIST_OVERFLOW (some atom has more than cap neighbours; counts is
  * still complete), MD_ERR_CUDA; md_last_error(NULL) gives the message.
+ * Cite: no paper passage has an allocation-free variant; the sets are those
+ * of Sec. III.B (numneigh[i], neighbors[i][jj]).
  */
 #define MD_NOALLOC_MAX_ATOMS 65536
 #define MD_NOALLOC_MAX_BINS 32768
 md_status md_neighbors_noalloc(int64_t n, const double *x, const double *box, double rl, int32_t *counts,
                                int32_t *nbr, int32_t cap, void *stream);
 
-/* Synchronise the handle's stream and return (and clear) the latched device status. */
+/*
+ * The set-up mini-benchmark's measurements (md_autotune): one row per force
+ * kernel variant it timed on this handle, in the order timed.  rows: host
+ * array of cap entries; *n_out (host) = rows written (0 before any
+ * md_autotune call, or after one answered from its cache file).
+ * Cite: Sec. III.B (the timed choice between the force-kernel variants).
+ */
+typedef struct {
+    int32_t tpa, list, block, vec; /* the variant (list: md_listkind)          */
+    double ms;                     /* median milliseconds per force pass       */
+} md_tune_row;
+md_status md_autotune_table(md_system *h, md_tune_row *rows, int32_t cap, int32_t *n_out);
+
+/*
+ * The device's own ceilings, measured by short probe kernels on `stream`:
+ * FP32 and FP64 fused multiply-add throughput (2 flops per FMA); random
+ * 16-byte gathers from an L2-resident array of 2^20 records driven by a
+ * streamed list of 2^26 indices (the access shape of the neighbour loop with
+ * no locality between lanes); a streaming device-to-device copy (read plus
+ * written bytes).  Allocates about 1.3 GB of device memory for the duration
+ * of the call and synchronises the stream.  out: host.
+ * Cite: no paper passage -- measurement only (the ceilings against which the
+ * force pass's throughput is reported).
+ */
+typedef struct {
+    double fp32_fma_tflops;
+    double fp64_fma_tflops;
+    double l2_gather_gps;      /* 10^9 gathers per second            */
+    double l2_gather_gbs;      /* gathered bytes, 10^9 per second    */
+    double index_stream_gbs;   /* the index stream's HBM bytes       */
+    double hbm_copy_gbs;
+} md_ceilings;
+md_status md_probe_ceilings(void *stream, md_ceilings *out);
+
+/*
+ * The library's FP64 reciprocal (op 0) and reciprocal square root (op 1) --
+ * Newton-Raphson steps from the FP32 hardware approximations, used by the
+ * FP64 force passes -- applied to x[n] (device), results in y[n] (device), on
+ * `stream`.  For tests that hold them to an error bound against the
+ * correctly rounded operations; valid for FLT_MIN < x < FLT_MAX.
+ * Cite: no paper passage -- test hook.
+ */
+md_status md_probe_fp64_math(int32_t op, int64_t n, const double *x, double *y, void *stream);
+
+/* Synchronise the handle's stream and return (and clear) the latched device status.
+ * Cite: no paper passage -- library plumbing (error reporting). */
 md_status md_sync_status(md_system *h);
 
-/* Message for the most recent failure on h (NULL: the last failure without a handle). */
+/* Message for the most recent failure on h (NULL: the last failure without a handle).
+ * Cite: no paper passage -- library plumbing. */
 const char *md_last_error(md_system *h);
 
 #ifdef __cplusplus

@@ -8,6 +8,8 @@ simulations on GPU-based clusters" (LAMMPS_CUDA).
 """
 from ._build import build as build_library  # noqa: F401
 from ._lib import load as load_library  # noqa: F401
-from .system import EAMForces, LJForces, MDError, System, lj_params, pairs_to_matrix  # noqa: F401
+from .system import (EAMForces, LJForces, MDError, System, fp64_math, lj_params, pairs_to_matrix,  # noqa: F401
+                     probe_ceilings)
 
-__all__ = ["System", "LJForces", "EAMForces", "MDError", "lj_params", "pairs_to_matrix", "build_library", "load_library"]
+__all__ = ["System", "LJForces", "EAMForces", "MDError", "lj_params", "pairs_to_matrix", "build_library", "load_library",
+           "probe_ceilings", "fp64_math"]

@@ -20,7 +20,7 @@ EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "
            "md_energy_virial", "md_get_state", "md_set_state", "md_set_params", "md_forces_backward",
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
            "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather", "md_set_staging",
-           "md_cell_forces")
+           "md_cell_forces", "md_autotune_table", "md_probe_ceilings", "md_probe_fp64_math")
 
 
 class MdConfig(ctypes.Structure):
@@ -38,6 +38,17 @@ class MdInfo(ctypes.Structure):
                 ("vec", ctypes.c_int32), ("max_count", ctypes.c_int32), ("list_entries", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("bins", ctypes.c_int32 * 3), ("tile_atoms", ctypes.c_int32),
                 ("tiles_staged", ctypes.c_int32), ("n_tiles_force", ctypes.c_int32)]
+
+
+class MdTuneRow(ctypes.Structure):
+    _fields_ = [("tpa", ctypes.c_int32), ("list", ctypes.c_int32), ("block", ctypes.c_int32), ("vec", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
+class MdCeilings(ctypes.Structure):
+    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
+                ("l2_gather_gps", ctypes.c_double), ("l2_gather_gbs", ctypes.c_double),
+                ("index_stream_gbs", ctypes.c_double), ("hbm_copy_gbs", ctypes.c_double)]
 
 
 _lib = None
@@ -80,6 +91,11 @@ def load(build_if_missing: bool = True):
         "md_sync_status": [vp],
         "md_time_force": [vp, i32, i32, P(d), P(d)],
         "md_time_gather": [vp, i32, i32, P(d)],
+        "md_set_staging": [vp, i32],
+        "md_cell_forces": [vp, vp, i32, P(d)],
+        "md_autotune_table": [vp, P(MdTuneRow), i32, P(i32)],
+        "md_probe_ceilings": [vp, P(MdCeilings)],
+        "md_probe_fp64_math": [i32, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -46,6 +46,7 @@ struct md_system {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t gp_part_size = 0;
+    std::vector<md_tune_row> tune;  // the last md_autotune's timings
     std::string err;
 };
 
@@ -890,8 +891,10 @@ md_status md_autotune(md_system *h, const char *cache_path) {
             const size_t bar = line.find('|');
             if (bar == std::string::npos || line.substr(0, bar) != key) continue;
             int t = 0, l = 0, b = 0, q = 0;
-            if (sscanf(line.c_str() + bar + 1, "%d %d %d %d", &t, &l, &b, &q) == 4)
+            if (sscanf(line.c_str() + bar + 1, "%d %d %d %d", &t, &l, &b, &q) == 4) {
+                h->tune.clear();
                 return md_set_kernel(h, t, (md_listkind)l, b, q);
+            }
         }
     }
     std::vector<int> lists;
@@ -903,6 +906,7 @@ md_status md_autotune(md_system *h, const char *cache_path) {
     CK(h, cudaEventCreate(&e1));
     double best = 1e300;
     int bt = 1, bl = MD_LIST_FULL, bb = 256, bq = 1;
+    h->tune.clear();
     for (int l : lists)
         for (int t : {1, 2, 4, 8, 16, 32})
             for (int q : {1, 2, 4})
@@ -927,6 +931,7 @@ md_status md_autotune(md_system *h, const char *cache_path) {
                     ms.push_back(m);
                 }
                 std::sort(ms.begin(), ms.end());
+                h->tune.push_back(md_tune_row{t, l, b, q, (double)ms[2]});
                 if (ms[2] < best) { best = ms[2]; bt = t; bl = l; bb = b; bq = q; }
             }
     cudaEventDestroy(e0);
@@ -937,6 +942,14 @@ md_status md_autotune(md_system *h, const char *cache_path) {
         std::ofstream outf(cache_path, std::ios::app);
         outf << key << "|" << bt << " " << bl << " " << bb << " " << bq << " " << best << "\n";
     }
+    return MD_OK;
+}
+
+md_status md_autotune_table(md_system *h, md_tune_row *rows, int32_t cap, int32_t *n_out) {
+    if (!h || !n_out || cap < 0 || (cap > 0 && !rows)) return fail(h, MD_ERR_INVALID, "bad argument");
+    const int n = std::min<int>(cap, (int)h->tune.size());
+    for (int k = 0; k < n; ++k) rows[k] = h->tune[k];
+    *n_out = n;
     return MD_OK;
 }
 

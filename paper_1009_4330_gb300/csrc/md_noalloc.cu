@@ -1,15 +1,16 @@
 // md_noalloc.cu -- md_neighbors_noalloc: the neighbour-list build for a
 // single periodic box without any device allocation.
 //
-// Who needs it: code that may not call cudaMalloc -- work issued while a
-// stream is being captured into a CUDA graph (allocation calls are not
-// allowed during capture), hosts whose device memory is owned entirely by
-// another allocator (a framework's caching pool, a fixed arena), and
-// latency-critical loops where an allocation, with the device-wide
-// synchronisation it may bring, is not acceptable.  Such callers can still
-// get the Verlet list of a small system: they pass the positions in and the
-// list buffers out, and every intermediate lives in one file-scope device
-// array of fixed size, reserved when the library is loaded on a device.
+// Who needs it: code that may not call cudaMalloc -- hosts whose device
+// memory is owned entirely by another allocator (a framework's caching pool,
+// a fixed arena sized at start-up), and latency-critical loops where an
+// allocation, with the device-wide synchronisation it may bring, is not
+// acceptable.  Such callers can still get the Verlet list of a small system:
+// they pass the positions in and the list buffers out, and every
+// intermediate lives in one file-scope device array of fixed size, reserved
+// when the library is loaded on a device.  The call reads an overflow flag
+// back and synchronises its stream, so it is not for use while that stream
+// is being captured into a CUDA graph.
 //
 // The steps are those of the handle-based rebuild (bin with edges >= the
 // list radius, counting sort, 27-cell stencil scan), simplified for one box:
@@ -221,13 +222,24 @@ extern "C" md_status md_neighbors_noalloc(int64_t n, const double *x, const doub
     c.n = a.n; c.cap = a.cap; c.rl2 = a.rl2; c.nbins = a.nbins;
     for (int q = 0; q < 3; ++q) { c.nb[q] = a.nb[q]; c.L[q] = a.L[q]; c.Linv[q] = a.Linv[q]; c.hinv[q] = a.hinv[q]; }
     cudaStream_t s = (cudaStream_t)stream;
-    const int g = (a.n + 255) / 256;
-    k_na_zero<<<(a.nbins + 255) / 256, 256, 0, s>>>(c);
-    k_na_bin<<<g, 256, 0, s>>>(c, x);
-    k_na_scan<<<1, 1024, 0, s>>>(c);
-    k_na_scatter<<<g, 256, 0, s>>>(c);
-    k_na_list<<<g, 256, 0, s>>>(c, counts, nbr);
-    if (cudaGetLastError() != cudaSuccess) return na_fail(MD_ERR_CUDA, "md_neighbors_noalloc: kernel launch failed");
+    const unsigned g = (unsigned)((a.n + 255) / 256);
+    // each launch's own status (cudaLaunchKernel returns it), so that an
+    // error left pending by other code is neither reported as ours nor cleared
+    void *a1[] = {&c};
+    void *a2[] = {&c, (void *)&x};
+    void *a3[] = {&c, &counts, &nbr};
+    const struct {
+        const void *fn;
+        unsigned grid, block;
+        void **args;
+    } launches[] = {{(const void *)k_na_zero, (unsigned)((a.nbins + 255) / 256), 256, a1},
+                    {(const void *)k_na_bin, g, 256, a2},
+                    {(const void *)k_na_scan, 1, 1024, a1},
+                    {(const void *)k_na_scatter, g, 256, a1},
+                    {(const void *)k_na_list, g, 256, a3}};
+    for (const auto &l : launches)
+        if (cudaLaunchKernel(l.fn, dim3(l.grid), dim3(l.block), l.args, 0, s) != cudaSuccess)
+            return na_fail(MD_ERR_CUDA, "md_neighbors_noalloc: kernel launch failed");
     int flag = 0;
     if (cudaMemcpyAsync(&flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

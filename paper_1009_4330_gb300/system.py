@@ -72,6 +72,7 @@ class System:
         h = ctypes.c_void_p()
         self._check(self._lib.md_create(ctypes.byref(cfg), _ptr(x), _ptr(v), _ptr(t), ctypes.byref(h)), None)
         self._h = h
+        self._version = 0  # bumped whenever positions or parameters change
         self.n = n
         self.n_rep = 1
         self.n_types = n_types
@@ -140,6 +141,7 @@ class System:
         h = ctypes.c_void_p()
         self._check(self._lib.md_batch_create(R, cfgs, px, pv, pt, ctypes.byref(h)), None)
         self._h = h
+        self._version = 0
         self.n = sum(a.shape[0] for a in xs)
         self.n_rep = R
         self.sizes = [a.shape[0] for a in xs]
@@ -186,6 +188,7 @@ class System:
 
     def step(self, nsteps=1, eager=False):
         """Advance nsteps velocity-Verlet steps (eager: without CUDA graphs, for profiling)."""
+        self._version += 1
         self._call("md_step_eager" if eager else "md_step", ctypes.c_int64(int(nsteps)))
 
     def energy_virial(self):
@@ -204,11 +207,13 @@ class System:
     def set_state(self, x=None, v=None):
         xd = _dev(x, torch.float64, (-1, 3)) if x is not None else None
         vd = _dev(v, torch.float64, (-1, 3)) if v is not None else None
+        self._version += 1
         self._call("md_set_state", _ptr(xd), _ptr(vd))
         torch.cuda.current_stream().synchronize()
 
     def set_params(self, params):
         p = np.ascontiguousarray(params, dtype=np.float64).ravel()
+        self._version += 1
         self._call("md_set_params", p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
     def backward(self, grad_f):
@@ -241,6 +246,15 @@ class System:
     def autotune(self, cache_path=None):
         self._call("md_autotune", cache_path.encode() if cache_path else None)
 
+    def autotune_table(self):
+        """The last autotune's timings: list of dicts (tpa, list, block, vec, ms), in the order timed."""
+        rows = (L.MdTuneRow * 256)()
+        n = ctypes.c_int32()
+        self._call("md_autotune_table", rows, ctypes.c_int32(256), ctypes.byref(n))
+        names = {L.MD_LIST_FULL: "full", L.MD_LIST_HALF: "half"}
+        return [{"tpa": r.tpa, "list": names.get(r.list, r.list), "block": r.block, "vec": r.vec, "ms": r.ms}
+                for r in rows[:n.value]]
+
     def set_kernel(self, tpa, list="full", block=128, vec=None):
         """Force-kernel variant; vec (list entries per thread per load) defaults to 4 for tpa <= 8, else 1."""
         if vec is None:
@@ -249,6 +263,11 @@ class System:
 
     def sync_status(self):
         self._call("md_sync_status")
+
+    @property
+    def version(self):
+        """Counter of changes to positions or parameters (steps, set_state, set_params)."""
+        return self._version
 
     def cell_forces(self, reps=0):
         """Forces (n,3) from the cell-list pass (no Verlet list) and, if reps > 0, its ms per pass."""
@@ -275,6 +294,33 @@ class System:
         return ms.value, by.value
 
 
+# -------------------------------------------------------------- probes --
+
+def probe_ceilings():
+    """The device's own ceilings (dict): FP32 / FP64 FMA TFLOP/s, random 16-byte
+    gathers from an L2-resident array (G/s and GB/s), streaming copy GB/s."""
+    _require_cuda()
+    lib = L.load()
+    out = L.MdCeilings()
+    st = lib.md_probe_ceilings(_stream_handle(), ctypes.byref(out))
+    if st != L.MD_OK:
+        raise MDError(st, lib.md_last_error(None).decode())
+    return {k: getattr(out, k) for k, _ in L.MdCeilings._fields_}
+
+
+def fp64_math(op, x):
+    """The library's FP64 reciprocal (op 'rcp') or reciprocal square root ('rsqrt') of a float64 CUDA tensor."""
+    _require_cuda()
+    lib = L.load()
+    xd = _dev(x, torch.float64)
+    y = torch.empty_like(xd)
+    st = lib.md_probe_fp64_math({"rcp": 0, "rsqrt": 1}[op], ctypes.c_int64(xd.numel()), _ptr(xd), _ptr(y),
+                                _stream_handle())
+    if st != L.MD_OK:
+        raise MDError(st, lib.md_last_error(None).decode())
+    return y
+
+
 # ------------------------------------------------------------------ autograd --
 
 def pairs_to_matrix(vals, nt):
@@ -286,6 +332,16 @@ def pairs_to_matrix(vals, nt):
             m[a, b] = m[b, a] = float(vals[k])
             k += 1
     return m
+
+
+def _check_fresh(ctx):
+    """The backward kernels differentiate at the system's CURRENT positions and
+    parameters: refuse if they changed after this forward (a step, set_state,
+    set_params, or another forward on the same system)."""
+    if ctx.system.version != ctx.version:
+        raise MDError(int(L.MD_ERR_INVALID),
+                      "backward of a stale forward: the system's positions or parameters changed since "
+                      f"(version {ctx.version} at the forward, {ctx.system.version} now)")
 
 
 class LJForces(torch.autograd.Function):
@@ -308,6 +364,7 @@ class LJForces(torch.autograd.Function):
             system.set_state(x=x.detach())
         f = system.compute_forces()
         ctx.system = system
+        ctx.version = system.version
         ctx.has_x = x is not None
         ctx.x_dtype = x.dtype if x is not None else None
         ctx.p_dtype = (eps_pairs.dtype, sig_pairs.dtype, eps_pairs.device, sig_pairs.device)
@@ -316,6 +373,7 @@ class LJForces(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_f):
         system = ctx.system
+        _check_fresh(ctx)
         nt = system.n_types
         gx, gp = system.backward(grad_f.contiguous())
         gp = gp.cpu().numpy()
@@ -347,6 +405,7 @@ class EAMForces(torch.autograd.Function):
             system.set_state(x=x.detach())
         f = system.compute_forces()
         ctx.system = system
+        ctx.version = system.version
         ctx.has_x = x is not None
         ctx.x_dtype = x.dtype if x is not None else None
         ctx.p_dtype = (params.dtype, params.device)
@@ -354,6 +413,7 @@ class EAMForces(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_f):
+        _check_fresh(ctx)
         gx, gp = ctx.system.backward(grad_f.contiguous())
         pdt, pdev = ctx.p_dtype
         gxo = gx.to(ctx.x_dtype) if ctx.has_x else None

@@ -68,7 +68,9 @@ def margin_ok(x, box, rl, idx=None, margin=1e-9):
     return oracle.min_gap(x, box, rl, idx) > margin
 
 
-# the general parity inputs keep every pair at least this far (relative) from
-# rc; pairs nearer rc, which the mixed pass decides in FP64, have their own
-# cases in test_gpu_cutoff.py
-RC_MARGIN_MIXED = 1e-6
+# The cell-list force pass (md_cell_forces, a measured design alternative
+# that reads no Verlet list) decides every pair's cut-off in FP32; the
+# unshifted LJ force jumps at rc, so its parity inputs keep pairs this far
+# (relative) from rc.  The list-based passes decide pairs near rc in FP64 and
+# take unfiltered inputs.
+RC_MARGIN_CELL_PASS = 1e-6

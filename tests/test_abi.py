@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "md.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(md_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(md_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -117,6 +117,28 @@ def test_ctypes_mirrors_match_the_c_header(tmp_path):
     assert int(out[1]) == ctypes.sizeof(_lib.MdInfo)
     for f, off in zip(fields, out[2:]):
         assert int(off) == getattr(_lib.MdInfo, f).offset, f
+    # the other structs of the header
+    src2 = tmp_path / "probe2.c"
+    src2.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"md.h\"\nint main(void) {\n"
+                    "  printf(\"%zu %zu %zu\\n\", sizeof(md_tune_row), offsetof(md_tune_row, ms), sizeof(md_ceilings));\n"
+                    "  return 0;\n}\n")
+    exe2 = tmp_path / "probe2"
+    subprocess.check_call([cc, "-I", inc, str(src2), "-o", str(exe2)])
+    a, b, c = (int(t) for t in subprocess.check_output([str(exe2)], text=True).split())
+    assert a == ctypes.sizeof(_lib.MdTuneRow) and b == _lib.MdTuneRow.ms.offset
+    assert c == ctypes.sizeof(_lib.MdCeilings)
+
+
+def test_every_entry_point_cites_its_passage():
+    # each declaration's comment block names the paper passage that defines the
+    # operation, or says that no passage does (plumbing, measurement, tests)
+    src = open(HEADER).read()
+    decls = [m for m in re.finditer(r"^(?:md_status|const char \*)\s*(md_[a-z_0-9]+)\s*\(", src, flags=re.M)]
+    prev = 0
+    for m in decls:
+        block = src[prev:m.start()]
+        assert "Cite:" in block, m.group(1)
+        prev = m.end()
 
 
 def test_empty_and_oversized_systems_rejected_on_host(lib):

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import (RC_MARGIN_MIXED, TOL_FP64, TOL_MIXED, assert_lists_equal, gpu_lists, lj_case, margin_ok,
+from gpu_util import (TOL_FP64, TOL_MIXED, assert_lists_equal, gpu_lists, lj_case, margin_ok,
                       rel_maxnorm, wrap_diff)
 
 pytestmark = pytest.mark.gpu
@@ -97,7 +97,7 @@ def test_nve_drift_below_bound(prec):
 def eam_case():
     d = synth.config2(cells=8, displacement=0.1)  # 2,048 atoms
     x, box = d["x"], d["box"]
-    assert margin_ok(x, box, d["rc"] + d["skin"]) and margin_ok(x, box, d["rc"], margin=RC_MARGIN_MIXED)
+    assert margin_ok(x, box, d["rc"] + d["skin"])
     f, e, w, rho, fp = oracle.eam(x, box, d["eam"])
     return dict(d, f=f, e=e, w=w, nbr=oracle.neighbors(x, box, d["rc"] + d["skin"]),
                 ke=oracle.kinetic(d["v"], d["mass"], ftm2v=d["ftm2v"]))

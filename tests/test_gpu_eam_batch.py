@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import RC_MARGIN_MIXED, margin_ok, rel_maxnorm
+from gpu_util import margin_ok, rel_maxnorm
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +21,7 @@ def replicas():
         x, box = synth.fcc_lattice(cells, cells, cells, 3.615)
         x = synth.displace(x, box, 0.08, 50 + k)
         v = synth.maxwell_boltzmann(x.shape[0], 300.0, MASS, 60 + k, kb=synth.KB_METAL, ftm2v=synth.FTM2V_METAL)
-        assert margin_ok(x, box, P[0] + SKIN) and margin_ok(x, box, P[0], margin=RC_MARGIN_MIXED)
+        assert margin_ok(x, box, P[0] + SKIN)
         out.append({"x": x, "v": v, "box": box})
     return out
 
