@@ -385,3 +385,27 @@ def test_autotune_picks_a_valid_layout_and_keeps_parity(tmp_path):
     with lj_system(d, "mixed", 1, lst="auto") as s:
         s.autotune(cache)  # cache hit
         assert s.info()["tpa"] == inf["tpa"]
+
+
+def test_backward_of_a_stale_forward_is_refused(ka_case):
+    # the backward kernels differentiate at the system's current state: after a
+    # step (or new parameters) the recorded forward no longer matches, and the
+    # autograd functions refuse instead of returning wrong gradients
+    import torch
+    from paper_1009_4330_gb300 import LJForces, MDError, System
+    c = ka_case
+    v = np.zeros_like(c["x"])
+    ep = torch.tensor([1.0, 1.5, 0.5], dtype=torch.float64, requires_grad=True)
+    sp = torch.tensor([1.0, 0.8, 0.88], dtype=torch.float64, requires_grad=True)
+    with System.lj(c["x"], v, c["box"], eps=c["e0"], sig=c["s0"], types=c["t"], n_types=2, cutoff=RC, skin=SKIN,
+                   dt=DT, mass=[1.0, 1.0], precision="fp64", tpa=4) as s:
+        f = LJForces.apply(s, None, ep, sp)
+        s.step(1)
+        with pytest.raises(MDError, match="stale"):
+            f.sum().backward()
+        f = LJForces.apply(s, None, ep, sp)
+        f2 = LJForces.apply(s, None, ep * 1.01, sp)  # a second forward re-parameterises the system
+        with pytest.raises(MDError, match="stale"):
+            f.sum().backward()
+        f2.sum().backward()  # the latest forward is still current
+        assert ep.grad is not None and torch.isfinite(ep.grad).all()
