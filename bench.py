@@ -225,15 +225,23 @@ def nve_drift(s, n, steps=DRIFT_STEPS, every=DRIFT_EVERY):
             "steps": steps, "sampled_every": every, "e_per_atom_start": es[0]}
 
 
+EQUILIBRATION_STEPS = 500
+
+
 def accuracy_report(s, d):
-    """Accuracy stated with the throughput, on the bench workload itself:
-    (1) mixed-precision forces against the plain FP64 GPU path (which the
-    tests hold to the FP64 oracle at 1e-12) at the state after the timed
-    steps; (2) NVE drift over 1,000 further steps of the mixed run, and over
-    1,000 steps of the plain FP64 path from the same state (least-squares
-    slope of the shifted total energy per atom, x 1000)."""
+    """Accuracy stated with the throughput, on the bench workload itself,
+    independent of --steps: the run is first carried to at least 500 steps
+    from its fcc start (the lattice melts in the first ~200 steps, while many
+    pairs cross the cut-off at once), then (1) mixed-precision forces against
+    the plain FP64 GPU path (which the tests hold to the FP64 oracle at
+    1e-12) at that state; (2) NVE drift over 1,000 further steps of the mixed
+    run, and over 1,000 steps of the plain FP64 path from the same state
+    (least-squares slope of the shifted total energy per atom, x 1000)."""
     from paper_1009_4330_gb300 import System
     n = d["x"].shape[0]
+    done = s.info()["steps"]
+    if done < EQUILIBRATION_STEPS:
+        s.step(EQUILIBRATION_STEPS - done)
     x, v, _ = s.state()
     f_mixed = s.compute_forces().cpu().numpy()
     with System.lj(x, v, d["box"], cutoff=d["rc"], skin=d["skin"], dt=d["dt"], mass=1.0, precision="fp64",
@@ -245,7 +253,8 @@ def accuracy_report(s, d):
     return {"mixed_force_rel_maxnorm_vs_fp64": err, "force_tolerance": 1e-5,
             "nve_drift_mixed": drift_mixed, "nve_drift_fp64": drift64, "drift_bound": 1e-4,
             "drift_definition": "least-squares slope of E_tot/N vs step, x 1000",
-            "energy": "shifted LJ (continuous at rc)", "state": "from the state after the timed steps"}
+            "energy": "shifted LJ (continuous at rc)",
+            "state": f"the bench run carried to step {max(done, EQUILIBRATION_STEPS)} from its fcc start"}
 
 
 def e2e_run(s, d, K):
@@ -393,9 +402,17 @@ def roofline_of(f_ms, f_bytes, entries, g_ms, ceil, peak, peak_kind, traffic):
     if g_ms:
         ceilings["access_pattern_twin"] = {"twin_ms": g_ms, "frac": g_ms / f_ms,
                                            "note": "the same list stream and record gathers, no arithmetic"}
+    if ceil and ceilings["l2_gather"]["frac"] > 1.0:
+        ceilings["l2_gather"]["note"] = ("above the random-gather probe: the pass's gathers share records between "
+                                         "neighbouring atoms and hit L1 (the twin measures its own pattern)")
     out["ceilings"] = ceilings
-    fr = {k: v["frac"] for k, v in ceilings.items() if isinstance(v, dict) and "frac" in v}
-    out["binding"] = max(fr, key=fr.get) if fr else "hbm"
+    # the binding ceiling: the access pattern's own (the twin) when measured,
+    # else the largest fraction among the probes it does not exceed
+    if g_ms:
+        out["binding"] = "access_pattern_twin"
+    else:
+        fr = {k: v["frac"] for k, v in ceilings.items() if isinstance(v, dict) and "frac" in v and v["frac"] <= 1.0}
+        out["binding"] = max(fr, key=fr.get) if fr else "hbm"
     return out
 
 
@@ -486,7 +503,8 @@ def force_arm(s, ceil, prec):
     fms, fby = s.time_force(3, 10)
     inf = s.info()
     out = {"force_ms": fms, "force_GBs": fby / (fms / 1000) / 1e9}
-    if ceil and s.potential == "lj" and inf["list"] == "full":
+    if ceil and s.potential == "lj":
+        # per list entry the pair term is evaluated once, full or half list
         if prec == "fp64":
             tf = FP64_OPS_PER_ENTRY * inf["list_entries"] / (fms / 1000) / 1e12
             out["fp64_TFLOPs"] = tf

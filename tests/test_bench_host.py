@@ -114,5 +114,8 @@ def test_roofline_names_the_binding_ceiling():
     assert r["achieved"] == pytest.approx(3000.0) and r["frac"] == pytest.approx(3000.0 / 6800.0)
     assert r["ceilings"]["l2_gather"]["achieved_Ggathers_s"] == pytest.approx(600.0)
     assert r["ceilings"]["access_pattern_twin"]["frac"] == pytest.approx(0.9)
-    assert r["binding"] == "l2_gather"  # 1.2 of the random-gather probe
+    assert r["binding"] == "access_pattern_twin"
+    assert "note" in r["ceilings"]["l2_gather"]  # 1.2 of the random-gather probe: not a ceiling of this pattern
+    r = b.roofline_of(0.1, 300e6, 60e6, None, ceil, 6800.0, "measured", None)
+    assert r["binding"] == "hbm"  # l2_gather exceeded, fp32 0.2, hbm 0.44
     assert r["traffic"] is None and r["traffic_source"] is None
