@@ -49,10 +49,12 @@ def parse():
     ap.add_argument("--block", type=int, default=128, help="force-kernel threads per block when --tpa is given")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
-    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch"],
+    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch", "lj4000"],
                     help="run one small workload for a profiler and exit: 'build' = LJ liquid (--cells, --rc), "
                          "100 steps to melt the lattice, then two list rebuilds; 'eam_backward' = EAM metal "
-                         "(--cells), forces + backward twice")
+                         "(--cells), forces + backward twice; 'lj4000' = the 4,000-atom FP64 liquid, 100 steps "
+                         "in one md_step graph launch and 100 eager steps (kernels launched one by one), both "
+                         "timed")
     ap.add_argument("--rc", type=float, default=2.5, help="LJ cut-off of --profile build")
     return ap.parse_args()
 
@@ -708,6 +710,18 @@ def run_profile(args):
     import torch
     import synth
     from paper_1009_4330_gb300 import System, lj_params
+    if args.profile == "lj4000":
+        c0 = synth.config0()
+        s = System.lj(c0["x"], c0["v"], c0["box"], cutoff=2.5, skin=0.3, dt=0.005, mass=1.0, precision="fp64",
+                      tpa=args.tpa or 8, list="full")
+        s.step(20)
+        ms_graph, i0, i1, _ = time_steps(s, 100, 5)
+        ms_eager, j0, j1, _ = time_steps(s, 100, 5, eager=True)
+        print(json.dumps({"ms_per_step_graph": ms_graph / 100, "ms_per_step_eager": ms_eager / 100,
+                          "rebuilds_graph": i1["rebuilds"] - i0["rebuilds"], "rebuilds_eager": j1["rebuilds"] - j0["rebuilds"],
+                          "info": i1}))
+        s.close()
+        return
     if args.profile == "build":
         s, d = make_lj(synth, args.cells, args.rc, "mixed", tpa=args.tpa or (1 if args.rc < 3 else 4), lst="full")
         s.step(100)

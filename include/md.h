@@ -403,6 +403,73 @@ md_status md_probe_ceilings(void *stream, md_ceilings *out);
  */
 md_status md_probe_fp64_math(int32_t op, int64_t n, const double *x, double *y, void *stream);
 
+/*
+ * ----- Spatial decomposition (paper Sec. V) -------------------------------
+ * A box cut into sub-domains, one handle per sub-domain: each handle holds
+ * the atoms it owns plus ghost copies of the atoms of neighbouring
+ * sub-domains within the list radius of its boundaries.  Every step the
+ * owners' new positions are packed into buffers ON THE DEVICE, sent, and
+ * unpacked into the ghosts ON THE DEVICE (Sec. V: the communication buffers
+ * are built on the GPU, transferred, and only opened there); EAM adds the
+ * ghosts' F'(rho) after the density pass; with Newton's third law across
+ * the boundary, the forces accumulated on ghosts go back to their owners.
+ * These entry points are the device side of that exchange; the transport
+ * (MPI, NCCL, host copies) and the choice of ghosts belong to the caller.
+ *
+ * Quantities, as bit flags; a row holds the selected ones in this order.
+ */
+#define MD_HALO_X 1   /* position, 3 doubles: absolute, wrapped into the handle's box (+ shift when packing) */
+#define MD_HALO_V 2   /* velocity, 3 doubles                                                          */
+#define MD_HALO_F 4   /* force, 3 doubles, as last stored                                             */
+#define MD_HALO_FP 8  /* EAM only: F'(rho), 1 double, from the last density pass                      */
+#define MD_HALO_EV 16 /* pack only: the atom's 8 terms of the last md_energy_virial (Epot share,      */
+                      /* kinetic energy, virial share Wxx Wyy Wzz Wxy Wxz Wyz)                        */
+
+/*
+ * Pack rows of the selected quantities of atoms idx[k] (device int32, m of
+ * them, indices in the caller's original order) into buf (device,
+ * m x width doubles).  shift: host double[3] added to packed positions (the
+ * offset from this sub-domain's frame to the receiver's), or NULL.  An index
+ * outside [0, n) latches an error reported by md_vv(MD_VV_DISP) or
+ * md_sync_status, and its row is filled with NaN.  Asynchronous.
+ * Cite: Sec. V (each processor packs the data of the particles within the
+ * interaction range of a neighbouring sub-box into a buffer, built on the GPU).
+ */
+md_status md_halo_pack(md_system *h, const int32_t *idx, int64_t m, int32_t what, const double *shift, double *buf);
+
+/*
+ * Unpack rows (layout as md_halo_pack) into atoms idx[k].  X sets positions
+ * (absolute coordinates in this handle's box; each atom keeps its cell and
+ * list entries, so it must stay within skin/2 of its position at the last
+ * build -- check with md_vv(MD_VV_DISP) and rebuild otherwise); V sets
+ * velocities; F sets forces, or adds them if accumulate != 0 (F alone);
+ * FP sets F'(rho) (EAM).  EV cannot be unpacked.  Asynchronous.
+ * Cite: Sec. V (received buffers are transferred to the GPU and only
+ * opened there).
+ */
+md_status md_halo_unpack(md_system *h, const int32_t *idx, int64_t m, int32_t what, int32_t accumulate,
+                         const double *buf);
+
+/*
+ * One phase of a velocity-Verlet step taken apart, so that a decomposed
+ * step can exchange data between phases:
+ *   MD_VV_DRIFT   v += (dt/2) a(F_stored); x += dt v (FP64); FP32 records refreshed
+ *   MD_VV_DISP    out[0] (HOST) = largest |x - x_build| of any atom of the handle
+ *                 (synchronises; also reports an out-of-range halo index)
+ *   MD_VV_DENSITY EAM: rho and F'(rho) of every atom over the current list
+ *   MD_VV_FORCE   forces at the current positions, stored (EAM: from F'(rho)
+ *                 as it stands, i.e. after MD_VV_DENSITY and the ghosts' F')
+ *   MD_VV_KICK    v += (dt/2) a(F_stored)
+ * A step is DRIFT, [exchange X], DISP (rebuild if any atom anywhere moved
+ * more than skin/2), [DENSITY, exchange FP], FORCE, [reverse F], KICK: the
+ * same arithmetic as md_step, without its CUDA graph.  out is only used by
+ * MD_VV_DISP.
+ * Cite: Sec. II (velocity-Verlet NVE on the GPU), Sec. V (the exchange
+ * points of a spatially decomposed step).
+ */
+typedef enum { MD_VV_DRIFT = 0, MD_VV_DISP = 1, MD_VV_DENSITY = 2, MD_VV_FORCE = 3, MD_VV_KICK = 4 } md_vv_phase;
+md_status md_vv(md_system *h, int32_t phase, double *out);
+
 /* Synchronise the handle's stream and return (and clear) the latched device status.
  * Cite: no paper passage -- library plumbing (error reporting). */
 md_status md_sync_status(md_system *h);

@@ -678,8 +678,9 @@ __global__ void k_kick(View V, KArgs a) {
         if (p - R.atom0 < R.natoms) {
             const int n = V.n_pad;
             const int t = V.type[p];
-            if (a.mode == kModeStep || a.mode == kModeKickDry) {
-                const double c = (a.mode == kModeKickDry) ? 0.0 : (rem == 1 ? 0.5 : 1.0) * V.dt * s_ftm[t];
+            if (a.mode == kModeStep || a.mode == kModeKickDry || a.mode == kModeHalfKick) {
+                const double c = (a.mode == kModeKickDry) ? 0.0
+                                 : (a.mode == kModeHalfKick || rem == 1 ? 0.5 : 1.0) * V.dt * s_ftm[t];
                 V.v[p] += c * V.f[p];
                 V.v[n + p] += c * V.f[n + p];
                 V.v[2 * n + p] += c * V.f[2 * n + p];
@@ -1139,6 +1140,12 @@ void drift_sequence(const View &V, bool in_graph, std::vector<KCall> &seq) {
                             dim3((V.n_pad + 256 * kDriftPer - 1) / (256 * kDriftPer)), dim3(256), 0, a});
     else  // two atoms per thread
         seq.push_back(KCall{(const void *)k_drift<MD_PREC_MIXED>, dim3((V.n_pad / 2 + 255) / 256), dim3(256), 0, a});
+}
+
+void kick_sequence(const View &V, int mode, std::vector<KCall> &seq) {
+    KArgs a{};
+    a.mode = mode;
+    seq.push_back(KCall{(const void *)k_kick, dim3((V.n_pad + 255) / 256), dim3(256), 0, a});
 }
 
 void loop_init_sequence(const View &V, std::vector<KCall> &seq) {

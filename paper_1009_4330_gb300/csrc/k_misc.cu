@@ -1,6 +1,8 @@
 // k_misc.cu -- moving state between the caller's original order and the
 // library's cell-sorted order, deterministic energy/virial reduction, the LJ
 // backward (vector-Jacobian) kernel, and list export.
+#include <algorithm>
+
 #include "md_common.cuh"
 #include "md_kernels.h"
 
@@ -450,6 +452,124 @@ __global__ void k_neighbors_out(View V, int *counts, int *nbr, int cap) {
     }
 }
 
+
+// ------------------------------------------------------------------ halo ----
+// Device-side communication buffers of a spatial decomposition (paper
+// Sec. V: the buffers are built on the GPU and only opened there): rows of
+// the selected per-atom quantities of the atoms named by the caller's
+// indices, gathered from (pack) or scattered into (unpack) the cell-sorted
+// state through the inverse map of the last build.
+constexpr int kHaloX = 1, kHaloV = 2, kHaloF = 4, kHaloFP = 8, kHaloEV = 16;
+
+__device__ __forceinline__ int halo_slot(const View &V, const int *idx, long long k, long long n_real) {
+    const long long o = idx[k];
+    if (o < 0 || o >= n_real) {
+        latch_error(V.ctl, kErrConfig);
+        return -1;
+    }
+    return V.inv[o];
+}
+
+template <int PREC>
+__global__ void k_halo_pack(View V, const int *idx, long long m, int what, int width, double sx, double sy, double sz,
+                            long long n_real, double *buf) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
+        double *row = buf + k * width;
+        const int p = halo_slot(V, idx, k, n_real);
+        if (p < 0) {
+            for (int c = 0; c < width; ++c) row[c] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+            continue;
+        }
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        const int n = V.n_pad;
+        int c = 0;
+        if (what & kHaloX) {
+            double xa[3];
+            abs_pos<PREC>(V, R, p, xa);
+            const double sh[3] = {sx, sy, sz};
+            for (int a = 0; a < 3; ++a) {
+                const double L = R.L[a];
+                double w = xa[a] - floor(xa[a] * R.Linv[a]) * L;
+                if (w >= L) w -= L;
+                if (w < 0.0) w += L;
+                row[c++] = w + sh[a];
+            }
+        }
+        if (what & kHaloV) for (int a = 0; a < 3; ++a) row[c++] = V.v[a * n + p];
+        if (what & kHaloF) for (int a = 0; a < 3; ++a) row[c++] = V.f[a * n + p];
+        if (what & kHaloFP) row[c++] = PREC == MD_PREC_FP64 ? V.fp64[p] : (double)V.rec[p].w;
+        if (what & kHaloEV) for (int q = 0; q < 8; ++q) row[c++] = V.ev[(size_t)q * n + p];
+    }
+}
+
+template <int PREC>
+__global__ void k_halo_unpack(View V, const int *idx, long long m, int what, int width, int accumulate,
+                              long long n_real, const double *buf) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
+        const int p = halo_slot(V, idx, k, n_real);
+        if (p < 0) continue;
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        const int n = V.n_pad;
+        const double *row = buf + k * width;
+        int c = 0;
+        if (what & kHaloX) {
+            // position relative to the centre of the atom's cell at the last
+            // build, nearest periodic image (the atom keeps its cell and list)
+            const int b = V.bpk[p];
+            const int bc[3] = {unpack_bx(b), unpack_by(b), unpack_bz(b)};
+            double d[3];
+            for (int a = 0; a < 3; ++a) {
+                double t = row[c++] - ((double)bc[a] + 0.5) * R.h[a];
+                t -= R.L[a] * rint(t * R.Linv[a]);
+                d[a] = t;
+            }
+            if (PREC == MD_PREC_FP64) {
+                const double4_32a q = V.pos4[p];
+                V.pos4[p] = make_double4_32a(d[0], d[1], d[2], q.w);
+            } else {
+                for (int a = 0; a < 3; ++a) V.xr[a * n + p] = d[a];
+            }
+            const float4 r = V.rec[p];
+            V.rec[p] = make_float4((float)d[0], (float)d[1], (float)d[2], r.w);
+        }
+        if (what & kHaloV) for (int a = 0; a < 3; ++a) V.v[a * n + p] = row[c++];
+        if (what & kHaloF)
+            for (int a = 0; a < 3; ++a) {
+                const double f = row[c++];
+                V.f[a * n + p] = accumulate ? V.f[a * n + p] + f : f;
+            }
+        if (what & kHaloFP) {
+            if (PREC == MD_PREC_FP64) V.fp64[p] = row[c++];
+            else V.rec[p].w = (float)row[c++];
+        }
+    }
+}
+
+// largest squared displacement of any atom since the last build (the
+// rebuild criterion of a decomposed step, taken after the ghosts' update)
+template <int PREC>
+__global__ void k_disp_max(View V) {
+    float d2 = 0.f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V.n_pad; p += gridDim.x * blockDim.x) {
+        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        if (p - R.atom0 >= R.natoms) continue;
+        double x[3];
+        if (PREC == MD_PREC_FP64) {
+            const double4_32a q = V.pos4[p];
+            x[0] = q.x; x[1] = q.y; x[2] = q.z;
+        } else {
+            for (int a = 0; a < 3; ++a) x[a] = V.xr[a * V.n_pad + p];
+        }
+        const float4 b = V.recb[p];
+        const double ex = x[0] - b.x, ey = x[1] - b.y, ez = x[2] - b.z;
+        float e = (float)(ex * ex + ey * ey + ez * ez);
+        if (!(e <= 3.0e38f)) e = __int_as_float(0x7f800000);
+        d2 = fmaxf(d2, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&V.ctl->disp_max, __float_as_uint(d2));
+}
+
 // ------------------------------------------------------------ launchers ----
 
 static dim3 grid_of(int n, int b) { return dim3((unsigned)((n + b - 1) / b)); }
@@ -551,6 +671,36 @@ cudaError_t launch_backward(const View &V, const double *grad_f, double *grad_x,
 
 cudaError_t launch_neighbors_out(const View &V, int *counts, int *nbr, int cap, cudaStream_t s) {
     k_neighbors_out<<<grid_of(V.n_pad, 256), 256, 0, s>>>(V, counts, nbr, cap);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_halo_pack(const View &V, const int *idx, long long m, int what, int width, const double shift[3],
+                             long long n_real, double *buf, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const dim3 g((unsigned)std::min<long long>((m + 255) / 256, 8192));
+    if (V.prec == MD_PREC_FP64)
+        k_halo_pack<MD_PREC_FP64><<<g, 256, 0, s>>>(V, idx, m, what, width, shift[0], shift[1], shift[2], n_real, buf);
+    else
+        k_halo_pack<MD_PREC_MIXED><<<g, 256, 0, s>>>(V, idx, m, what, width, shift[0], shift[1], shift[2], n_real, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack(const View &V, const int *idx, long long m, int what, int width, int accumulate,
+                               long long n_real, const double *buf, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const dim3 g((unsigned)std::min<long long>((m + 255) / 256, 8192));
+    if (V.prec == MD_PREC_FP64)
+        k_halo_unpack<MD_PREC_FP64><<<g, 256, 0, s>>>(V, idx, m, what, width, accumulate, n_real, buf);
+    else
+        k_halo_unpack<MD_PREC_MIXED><<<g, 256, 0, s>>>(V, idx, m, what, width, accumulate, n_real, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_disp_max(const View &V, cudaStream_t s) {
+    const dim3 g((unsigned)std::min(std::max(1, (V.n_pad + 255) / 256), V.n_sm * 8));
+    if (V.prec == MD_PREC_FP64) k_disp_max<MD_PREC_FP64><<<g, 256, 0, s>>>(V);
+    else k_disp_max<MD_PREC_MIXED><<<g, 256, 0, s>>>(V);
     return cudaGetLastError();
 }
 

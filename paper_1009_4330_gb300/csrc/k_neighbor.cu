@@ -277,6 +277,7 @@ __device__ __forceinline__ void gather_slot(const View &V, const KArgs &a, int q
     }
     V.type[dst] = t;
     V.id[dst] = myid;
+    V.inv[R.orig0 + myid] = dst;
     V.bpk[dst] = pack_bins(bc[0], bc[1], bc[2]);
     const float4 rr = make_float4((float)xr[0], (float)xr[1], (float)xr[2], __int_as_float(t));
     V.rec[dst] = rr;

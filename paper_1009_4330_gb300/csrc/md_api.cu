@@ -542,6 +542,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.scan_blk, (size_t)(V.nbins_total + 4095) / 4096 + 1);
     AL(V.rep_base, (size_t)n_rep);
     AL(V.ncount, n);
+    AL(V.inv, (size_t)h->n_real);
     {
         // tile tables sized for the smallest tile (32 atoms)
         const size_t nt = (n + 31) / 32;
@@ -943,6 +944,88 @@ md_status md_autotune(md_system *h, const char *cache_path) {
         outf << key << "|" << bt << " " << bl << " " << bb << " " << bq << " " << best << "\n";
     }
     return MD_OK;
+}
+
+// ------------------------------------------------- spatial decomposition --
+
+static int halo_width(int what) {
+    return ((what & MD_HALO_X) ? 3 : 0) + ((what & MD_HALO_V) ? 3 : 0) + ((what & MD_HALO_F) ? 3 : 0) +
+           ((what & MD_HALO_FP) ? 1 : 0) + ((what & MD_HALO_EV) ? 8 : 0);
+}
+
+static md_status halo_check(md_system *h, const int32_t *idx, int64_t m, int32_t what, const void *buf) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    if (m < 0 || (m > 0 && (!idx || !buf))) return fail(h, MD_ERR_INVALID, "halo: null buffer or negative count");
+    if (what <= 0 || (what & ~(MD_HALO_X | MD_HALO_V | MD_HALO_F | MD_HALO_FP | MD_HALO_EV)))
+        return fail(h, MD_ERR_INVALID, "halo: unknown quantity bits 0x%x", (unsigned)what);
+    if ((what & MD_HALO_FP) && h->cfg.pot != MD_POT_EAM_FS)
+        return fail(h, MD_ERR_INVALID, "halo: F'(rho) exists only for EAM");
+    if (m > 0x7fffffffll) return fail(h, MD_ERR_INVALID, "halo: too many rows");
+    return MD_OK;
+}
+
+md_status md_halo_pack(md_system *h, const int32_t *idx, int64_t m, int32_t what, const double *shift, double *buf) {
+    md_status st = halo_check(h, idx, m, what, buf);
+    if (st) return st;
+    const double zero[3] = {0.0, 0.0, 0.0};
+    CK(h, launch_halo_pack(h->V, idx, m, what, halo_width(what), shift ? shift : zero, h->n_real, buf, h->s));
+    return MD_OK;
+}
+
+md_status md_halo_unpack(md_system *h, const int32_t *idx, int64_t m, int32_t what, int32_t accumulate,
+                         const double *buf) {
+    md_status st = halo_check(h, idx, m, what, buf);
+    if (st) return st;
+    if (what & MD_HALO_EV) return fail(h, MD_ERR_INVALID, "halo: per-atom energies can only be packed");
+    if (accumulate && what != MD_HALO_F) return fail(h, MD_ERR_INVALID, "halo: only forces can be accumulated");
+    CK(h, launch_halo_unpack(h->V, idx, m, what, halo_width(what), accumulate ? 1 : 0, h->n_real, buf, h->s));
+    return MD_OK;
+}
+
+md_status md_vv(md_system *h, int32_t phase, double *out) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    std::vector<KCall> seq;
+    switch (phase) {
+        case MD_VV_DRIFT: {
+            int first = 1;
+            CK(h, cudaMemcpyAsync(&h->d_ctl->first, &first, sizeof(int), cudaMemcpyHostToDevice, h->s));
+            drift_sequence(h->V, false, seq);
+            CK(h, run_seq(h, seq));
+            return MD_OK;
+        }
+        case MD_VV_DISP: {
+            if (!out) return fail(h, MD_ERR_INVALID, "md_vv MD_VV_DISP: null output");
+            CK(h, cudaMemsetAsync(&h->d_ctl->disp_max, 0, sizeof(unsigned), h->s));
+            CK(h, launch_disp_max(h->V, h->s));
+            Ctl c;
+            md_status st = read_ctl(h, &c);
+            if (st) return st;
+            float d2;
+            std::memcpy(&d2, &c.disp_max, sizeof(float));
+            out[0] = std::sqrt((double)d2);
+            if (c.err & kErrConfig) return fail(h, MD_ERR_INVALID, "an index passed to md_halo_* was out of range");
+            return MD_OK;
+        }
+        case MD_VV_DENSITY:
+        case MD_VV_FORCE: {
+            if (phase == MD_VV_DENSITY && h->cfg.pot != MD_POT_EAM_FS)
+                return fail(h, MD_ERR_INVALID, "md_vv MD_VV_DENSITY: EAM only");
+            force_sequence(h->V, kModeStoreF, h->block, false, seq);
+            if (h->cfg.pot == MD_POT_EAM_FS) {
+                // [density pass, force pass]: one or the other
+                if (phase == MD_VV_DENSITY) seq.resize(1);
+                else seq.erase(seq.begin());
+            }
+            CK(h, run_seq(h, seq));
+            return MD_OK;
+        }
+        case MD_VV_KICK:
+            kick_sequence(h->V, kModeHalfKick, seq);
+            CK(h, run_seq(h, seq));
+            return MD_OK;
+        default:
+            return fail(h, MD_ERR_INVALID, "md_vv: unknown phase %d", (int)phase);
+    }
 }
 
 md_status md_autotune_table(md_system *h, md_tune_row *rows, int32_t cap, int32_t *n_out) {

@@ -75,6 +75,7 @@ struct Ctl {                // device control block of a handle
     int need_maxneigh;      // largest list length seen by an overflowing build
     long long steps;        // completed time steps
     long long rebuilds;     // completed replica builds
+    unsigned disp_max;      // md_vv MD_VV_DISP: max squared displacement since the build, float bits
 };
 
 // Parameters of the potential, per ordered type pair p = ti * nt + tj.
@@ -120,6 +121,7 @@ struct View {
     double4_32a *pos4;        // [n_pad] cell-relative positions + type bits (fp64)
     double *v, *f;        // [3][n_pad]
     int *type, *id, *bpk; // type, index within the replica, packed bin coordinates
+    int *inv;             // [n_real] caller's (concatenated) atom index -> slot, rewritten at every build
     float4 *rec, *recb;   // float(xr) + type; the same at the last build
     // rebuild scratch
     double *tx, *tv;      // [3][n_pad] staged absolute positions / velocities (old order)
@@ -174,8 +176,9 @@ enum : int {
     kModeStoreF = 0,   // write F
     kModeStep = 1,     // inside md_step: full kick, or half kick + write F on the last step
     kModeEV = 2,       // write F and per-atom energy/virial/kinetic terms
-    kModeKickDry = 3   // the in-step memory traffic (v read + written) with a zero kick:
+    kModeKickDry = 3,  // the in-step memory traffic (v read + written) with a zero kick:
                        // used to time the force pass without changing the state
+    kModeHalfKick = 4  // k_kick only: v += (dt/2) a(F) from the stored F (md_vv MD_VV_KICK)
 };
 
 // ----------------------------------------------- block reductions (FP64) --

@@ -50,6 +50,15 @@ cudaError_t launch_eam_backward(const View &V, const double *grad_f, double *gra
                                 int nblocks_part, cudaStream_t s);
 cudaError_t launch_neighbors_out(const View &V, int *counts, int *nbr, int cap, cudaStream_t s);
 int backward_partial_blocks(const View &V);
+// halo buffers of a spatial decomposition (md_halo_pack / md_halo_unpack)
+cudaError_t launch_halo_pack(const View &V, const int *idx, long long m, int what, int width, const double shift[3],
+                             long long n_real, double *buf, cudaStream_t s);
+cudaError_t launch_halo_unpack(const View &V, const int *idx, long long m, int what, int width, int accumulate,
+                               long long n_real, const double *buf, cudaStream_t s);
+// largest squared displacement since the last build -> Ctl::disp_max
+cudaError_t launch_disp_max(const View &V, cudaStream_t s);
+// the kick kernel alone, epilogue `mode` (kModeHalfKick: v += dt/2 a from the stored F)
+void kick_sequence(const View &V, int mode, std::vector<KCall> &seq);
 
 // set the message md_last_error(NULL) returns (entry points without a handle)
 void set_last_error(const char *msg);

@@ -264,6 +264,40 @@ class System:
     def sync_status(self):
         self._call("md_sync_status")
 
+    # ------------------------------------------- spatial decomposition --
+    def halo_pack(self, idx, what, shift=None, out=None):
+        """Rows of the selected quantities (bit flags L.MD_HALO_*) of atoms idx
+        (int32 CUDA tensor, original order) packed on the device: (m, width)."""
+        idx = idx if idx.dtype == torch.int32 else idx.to(torch.int32)
+        m = int(idx.numel())
+        width = halo_width(what)
+        buf = out if out is not None else torch.empty((m, width), dtype=torch.float64, device="cuda")
+        sh = None
+        if shift is not None:
+            sh = np.ascontiguousarray(shift, dtype=np.float64)
+            self._keep_shift = sh
+        self._call("md_halo_pack", _ptr(idx), ctypes.c_int64(m), ctypes.c_int32(what),
+                   sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if sh is not None else None, _ptr(buf))
+        return buf
+
+    def halo_unpack(self, idx, what, buf, accumulate=False):
+        """Unpack rows (layout of halo_pack) into atoms idx on the device."""
+        idx = idx if idx.dtype == torch.int32 else idx.to(torch.int32)
+        m = int(idx.numel())
+        assert buf.shape[0] == m and buf.is_contiguous()
+        self._version += 1
+        self._call("md_halo_unpack", _ptr(idx), ctypes.c_int64(m), ctypes.c_int32(what),
+                   ctypes.c_int32(1 if accumulate else 0), _ptr(buf))
+
+    def vv(self, phase):
+        """One phase of a velocity-Verlet step (L.MD_VV_*); MD_VV_DISP returns the
+        largest displacement since the last build (synchronises)."""
+        out = ctypes.c_double(0.0)
+        if phase in (L.MD_VV_DRIFT, L.MD_VV_KICK):
+            self._version += 1
+        self._call("md_vv", ctypes.c_int32(phase), ctypes.byref(out))
+        return out.value if phase == L.MD_VV_DISP else None
+
     @property
     def version(self):
         """Counter of changes to positions or parameters (steps, set_state, set_params)."""
@@ -292,6 +326,12 @@ class System:
         by = ctypes.c_double()
         self._call("md_time_force", ctypes.c_int32(warmup), ctypes.c_int32(reps), ctypes.byref(ms), ctypes.byref(by))
         return ms.value, by.value
+
+
+def halo_width(what):
+    """doubles per row of a halo buffer for the quantity bits `what`"""
+    return (3 * bool(what & L.MD_HALO_X) + 3 * bool(what & L.MD_HALO_V) + 3 * bool(what & L.MD_HALO_F)
+            + bool(what & L.MD_HALO_FP) + 8 * bool(what & L.MD_HALO_EV))
 
 
 # -------------------------------------------------------------- probes --
