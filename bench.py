@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--block", type=int, default=128, help="force-kernel threads per block when --tpa is given")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
-    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch", "lj4000"],
+    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch", "lj4000", "force"],
                     help="run one small workload for a profiler and exit: 'build' = LJ liquid (--cells, --rc), "
                          "100 steps to melt the lattice, then two list rebuilds; 'eam_backward' = EAM metal "
                          "(--cells), forces + backward twice; 'lj4000' = the 4,000-atom FP64 liquid, 100 steps "
                          "in one md_step graph launch and 100 eager steps (kernels launched one by one), both "
-                         "timed")
+                         "timed; 'force' = LJ liquid (--cells), mixed, one thread per atom, full list: 50 steps, "
+                         "then the force pass and its memory-only twin, each launched twice")
     ap.add_argument("--rc", type=float, default=2.5, help="LJ cut-off of --profile build")
     return ap.parse_args()
 
@@ -353,7 +354,7 @@ def run_reference(args, ws, rank):
 # 500,000-atom case of this workload, scaled by atoms (the list length per
 # atom is the same).  Valid only for this kernel variant, as captured; for
 # any other variant roofline.traffic is null.
-K_LJ_TRAFFIC_PER_ATOM = (182.090752e6 + 4.451840e6) / 500000
+K_LJ_TRAFFIC_PER_ATOM = (182.553856e6 + 4.012544e6) / 500000
 K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full", "block": 128, "tile_atoms": 0}
 
 # FP32 operations per list entry of the mixed full-list pair loop (a fused
@@ -720,6 +721,15 @@ def run_profile(args):
         print(json.dumps({"ms_per_step_graph": ms_graph / 100, "ms_per_step_eager": ms_eager / 100,
                           "rebuilds_graph": i1["rebuilds"] - i0["rebuilds"], "rebuilds_eager": j1["rebuilds"] - j0["rebuilds"],
                           "info": i1}))
+        s.close()
+        return
+    if args.profile == "force":
+        s, d = make_lj(synth, args.cells, args.rc, "mixed", tpa=1, lst="full")
+        s.set_kernel(1, "full", 128, 4)
+        s.step(50)
+        f_ms, _ = s.time_force(0, 2)
+        g_ms = s.time_gather(0, 2)
+        print(json.dumps({"force_ms": f_ms, "twin_ms": g_ms, "atoms": int(d["x"].shape[0])}))
         s.close()
         return
     if args.profile == "build":

@@ -268,6 +268,8 @@ struct LJPair {
     using Acc = typename Pol<PREC>::Acc;
     const View *V;
     const real *lj1, *lj2, *lj3, *lj4, *off;
+    real c1, c2;  // one atom type (MT = 0): the coefficients in registers, not
+                  // re-read from shared memory for every pair
     real rc2;
     int ti, nt, n;
     real near_min;  // mixed: the smallest |r^2 - rc^2| of this thread's pairs
@@ -292,7 +294,8 @@ struct LJPair {
             const int tp = MT ? ti * nt + tj : 0;
             const real r2i = Pol<PREC>::rcp(r2);
             const real r6i = r2i * r2i * r2i;
-            real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
+            const real a1 = MT ? lj1[tp] : c1, a2 = MT ? lj2[tp] : c2;
+            real fpair = r6i * (a1 * r6i - a2) * r2i;
             fpair = in_cut(r2) ? fpair : (real)0;
             rx += dx * fpair; ry += dy * fpair; rz += dz * fpair;
             return;
@@ -301,7 +304,8 @@ struct LJPair {
             const int tp = MT ? ti * nt + tj : 0;
             const real r2i = Pol<PREC>::rcp(r2);
             const real r6i = r2i * r2i * r2i;
-            const real fpair = r6i * (lj1[tp] * r6i - lj2[tp]) * r2i;
+            const real a1 = MT ? lj1[tp] : c1, a2 = MT ? lj2[tp] : c2;
+            const real fpair = r6i * (a1 * r6i - a2) * r2i;
             const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
             rx += fxp; ry += fyp; rz += fzp;
             if (HALF) {
@@ -446,6 +450,7 @@ __global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, 
     LJPair<PREC, MT, HALF, EV> pr;
     pr.V = &V;
     pr.lj1 = s_lj1; pr.lj2 = s_lj2; pr.lj3 = s_lj3; pr.lj4 = s_lj4; pr.off = s_off;
+    pr.c1 = s_lj1[0]; pr.c2 = s_lj2[0];
     pr.rc2 = (PREC == MD_PREC_FP64) ? (real)V.rc2 : (real)V.rc2f;
     pr.nt = V.ntypes;
     pr.n = V.n_pad;
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(128) k_lj_cells(View V, KArgs a) {
     LJPair<MD_PREC_MIXED, MT, 0, 0> pr;
     pr.V = &V;
     pr.lj1 = s_lj1; pr.lj2 = s_lj2;
+    pr.c1 = s_lj1[0]; pr.c2 = s_lj2[0];
     pr.rc2 = V.rc2f;
     pr.nt = V.ntypes;
     pr.n = V.n_pad;
