@@ -611,6 +611,10 @@ def side_runs(synth, cells, K, W, ceil, tune_rc25=None):
     out["fp64_lj4000_100steps"] = {"value": 4000 * 100 / (ms / 1000), "ms_per_step": ms / 100, "tpa": i1["tpa"],
                                    "list": i1["list"]}
     s.close()
+    # spatial decomposition on this one GPU: the 864,000-atom liquid cut into 2
+    # slabs driven by two threads (every step: a host synchronisation for the
+    # global rebuild decision and device-packed halo exchanges)
+    out["decomposed_2slabs_lj864k"] = domain_timing(synth, cells)
     # force matching: forward forces + backward (positions and 6 parameters), 32,768 atoms
     out["force_matching_32768"] = force_matching_timing(synth)
     out["eam500000_fwd_bwd"] = eam_backward_timing(synth)
@@ -649,6 +653,41 @@ def cpu_celllist(synth, cells, steps=2):
     n = d["x"].shape[0]
     return {"value": n * steps / dt, "unit": "atom-timesteps/s", "cores": oracle.num_threads(),
             "kind": "O(N) cell-list FP64 velocity Verlet (host)", "sample": f"{steps} steps of the {n}-atom liquid"}
+
+
+def domain_timing(synth, cells, steps=100):
+    """atom-timesteps/s of the slab decomposition (2 sub-domains, threads on one
+    GPU), mixed precision, full lists: the cost of the exchanges and the
+    per-step rebuild decision, beside md_step's single graph launch."""
+    import threading
+    from paper_1009_4330_gb300.domain import SlabDomain, SlabLayout, ThreadComm, ThreadWorld, split_global
+    d = synth.config1(rc=2.5, cells=cells)
+    lay = SlabLayout(d["box"], 2, 2.8, 0.3)
+    parts = split_global(lay, d["x"], d["v"])
+    world = ThreadWorld(2)
+    res = [None, None]
+
+    def rank(r):
+        ids, xr, vr, tr = parts[r]
+        dom = SlabDomain(ThreadComm(world, r), lay, xr, vr, ids, tr, params=[1.0, 1.0], cutoff=2.5, skin=0.3,
+                         dt=0.005, mass=1.0, precision="mixed", list="full", tpa=1)
+        dom.step(10)
+        world.barrier.wait()
+        t0 = time.perf_counter()
+        dom.step(steps)
+        world.barrier.wait()
+        res[r] = (time.perf_counter() - t0, dom.rebuilds, dom.n_own)
+        dom.close()
+
+    th = [threading.Thread(target=rank, args=(r,)) for r in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    sec = max(r[0] for r in res)
+    n = d["x"].shape[0]
+    return {"value": n * steps / sec, "unit": UNIT, "ms_per_step": 1000 * sec / steps, "steps": steps,
+            "rebuilds": res[0][1], "owned": [r[2] for r in res], "timer": "host wall clock (threads)"}
 
 
 def force_matching_timing(synth, reps=20):

@@ -157,3 +157,55 @@ def test_halo_index_out_of_range_is_reported():
             s.vv(_lib.MD_VV_DISP)
         with pytest.raises(MDError):
             s.halo_unpack(bad[:1], _lib.MD_HALO_EV, torch.zeros((1, 8), dtype=torch.float64, device="cuda"))
+
+
+def _gloo_rank(rank, port, q):
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    import torch
+    import torch.distributed as dist
+    from paper_1009_4330_gb300.domain import SlabDomain, SlabLayout, TorchComm, split_global
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo")
+    x, v, box = lj_liquid()
+    lay = SlabLayout(box, 2, RC + SKIN, SKIN)
+    ids, xr, vr, tr = split_global(lay, x, v)[rank]
+    d = SlabDomain(TorchComm(), lay, xr, vr, ids, tr, params=[1.0, 1.0], cutoff=RC, skin=SKIN, dt=DT, mass=1.0,
+                   precision="fp64", list="half", tpa=4, newton=True)
+    d.step(60)
+    q.put((rank, d.owned_state()[:3], d.rebuilds))
+    d.close()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_processes_share_the_gpu():
+    # the multi-process path: two processes on the one GPU, each driving its
+    # slab's handle, exchanging device-packed buffers staged through host
+    # memory by gloo (no kernel waits on the other process)
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_gloo_rank, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = [q.get(timeout=600) for _ in range(2)]
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    x, v, box = lj_liquid()
+    n = x.shape[0]
+    xs, vs = np.full((n, 3), np.nan), np.full((n, 3), np.nan)
+    for _, (ids, xe, ve), rb in got:
+        xs[ids], vs[ids] = xe, ve
+        assert rb >= 3
+    ref = oracle.nve(x, v, box, 60, DT, RC, SKIN)
+    assert np.abs(wrap_diff(xs, ref["x"], box)).max() < 1e-9
+    assert np.abs(vs - ref["v"]).max() < 1e-9
