@@ -666,24 +666,31 @@ def domain_timing(synth, cells, steps=100):
     parts = split_global(lay, d["x"], d["v"])
     world = ThreadWorld(2)
     res = [None, None]
+    errors = []
 
     def rank(r):
-        ids, xr, vr, tr = parts[r]
-        dom = SlabDomain(ThreadComm(world, r), lay, xr, vr, ids, tr, params=[1.0, 1.0], cutoff=2.5, skin=0.3,
-                         dt=0.005, mass=1.0, precision="mixed", list="full", tpa=1)
-        dom.step(10)
-        world.barrier.wait()
-        t0 = time.perf_counter()
-        dom.step(steps)
-        world.barrier.wait()
-        res[r] = (time.perf_counter() - t0, dom.rebuilds, dom.n_own)
-        dom.close()
+        try:
+            ids, xr, vr, tr = parts[r]
+            dom = SlabDomain(ThreadComm(world, r), lay, xr, vr, ids, tr, params=[1.0, 1.0], cutoff=2.5, skin=0.3,
+                             dt=0.005, mass=1.0, precision="mixed", list="full", tpa=1)
+            dom.step(10)
+            world.barrier.wait()
+            t0 = time.perf_counter()
+            dom.step(steps)
+            world.barrier.wait()
+            res[r] = (time.perf_counter() - t0, dom.rebuilds, dom.n_own)
+            dom.close()
+        except Exception as e:  # reported below; the other thread's waits are released
+            errors.append(repr(e))
+            world.barrier.abort()
 
     th = [threading.Thread(target=rank, args=(r,)) for r in range(2)]
     for t in th:
         t.start()
     for t in th:
         t.join()
+    if errors or None in res:
+        return {"error": errors[0] if errors else "a sub-domain thread did not finish"}
     sec = max(r[0] for r in res)
     n = d["x"].shape[0]
     return {"value": n * steps / sec, "unit": UNIT, "ms_per_step": 1000 * sec / steps, "steps": steps,
