@@ -119,6 +119,29 @@ md_status md_create(const md_config *cfg, const double *x, const double *v, cons
 md_status md_batch_create(int32_t n_rep, const md_config *cfgs, const double *const *x,
                           const double *const *v, const int32_t *const *type, md_system **out);
 
+/*
+ * md_create with room for `capacity` atoms (>= cfg->n_atoms, host): the extra
+ * slots are inert padding until md_reset fills them.  For callers whose atom
+ * count changes from one list build to the next (a sub-domain of a spatial
+ * decomposition gains and loses atoms), so that they can keep one handle.
+ * Cite: Sec. V (each processor's sub-box gains and loses particles as they
+ * move); the capacity itself is library plumbing.
+ */
+md_status md_create_capacity(const md_config *cfg, int64_t capacity, const double *x, const double *v,
+                             const int32_t *type, md_system **out);
+
+/*
+ * Replace every atom of a single-system handle by n new ones -- x[n][3]
+ * (any real coordinates; wrapped into the box), v[n][3], type[n], device,
+ * original order -- keeping its box, parameters, force-kernel variant, CUDA
+ * graphs and device memory: the same state as a new handle with these atoms.
+ * n must not exceed the capacity the handle was created with (MD_ERR_UNSUPPORTED
+ * otherwise); batch handles are not supported.  Rebuilds the list and
+ * recomputes the forces; synchronises.
+ * Cite: Sec. V (atoms migrating between sub-boxes); library plumbing otherwise.
+ */
+md_status md_reset(md_system *h, int64_t n, const double *x, const double *v, const int32_t *type);
+
 /* Release the handle and all its device memory (synchronises its stream).
  * Cite: no paper passage -- library plumbing. */
 md_status md_destroy(md_system *h);

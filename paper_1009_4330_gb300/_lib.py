@@ -21,7 +21,7 @@ EXPORTS = ("md_create", "md_batch_create", "md_destroy", "md_build_neighbors", "
            "md_autotune", "md_set_kernel", "md_info", "md_get_neighbors", "md_sync_status", "md_last_error",
            "md_time_force", "md_step_eager", "md_neighbors_noalloc", "md_time_gather", "md_set_staging",
            "md_cell_forces", "md_autotune_table", "md_probe_ceilings", "md_probe_fp64_math", "md_halo_pack",
-           "md_halo_unpack", "md_vv")
+           "md_halo_unpack", "md_vv", "md_create_capacity", "md_reset")
 MD_HALO_X, MD_HALO_V, MD_HALO_F, MD_HALO_FP, MD_HALO_EV = 1, 2, 4, 8, 16
 MD_VV_DRIFT, MD_VV_DISP, MD_VV_DENSITY, MD_VV_FORCE, MD_VV_KICK = range(5)
 
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
         "md_halo_pack": [vp, vp, i64, i32, P(d), vp],
         "md_halo_unpack": [vp, vp, i64, i32, i32, vp],
         "md_vv": [vp, i32, P(d)],
+        "md_create_capacity": [P(MdConfig), i64, vp, vp, vp, P(vp)],
+        "md_reset": [vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

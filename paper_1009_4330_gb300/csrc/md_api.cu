@@ -47,6 +47,7 @@ struct md_system {
     cudaGraphExec_t exec = nullptr;
     size_t gp_part_size = 0;
     std::vector<md_tune_row> tune;  // the last md_autotune's timings
+    long long capacity = 0;         // atoms the slots hold (single system: md_create_capacity, md_reset)
     std::string err;
 };
 
@@ -390,7 +391,7 @@ static int initial_maxneigh(const std::vector<Rep> &reps, double rl) {
 }
 
 static md_status create_impl(int n_rep, const md_config *cfgs, const double *const *x, const double *const *v,
-                             const int32_t *const *type, md_system **out) {
+                             const int32_t *const *type, md_system **out, long long capacity = 0) {
     if (!out) return fail(nullptr, MD_ERR_INVALID, "null output handle");
     *out = nullptr;
     if (n_rep < 1) return fail(nullptr, MD_ERR_INVALID, "n_rep must be >= 1");
@@ -430,7 +431,9 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
         R.natoms = (int)cfgs[r].n_atoms;
         R.atom0 = atom0;
         R.tile0 = tile0;
-        R.ntiles = (R.natoms + 31) / 32;
+        // slots for `capacity` atoms (md_create_capacity): the ones past natoms are
+        // padding, which every kernel skips, until md_reset fills them
+        R.ntiles = (int)((std::max<long long>(R.natoms, capacity) + 31) / 32);
         R.orig0 = orig0;
         atom0 += R.ntiles * 32;
         tile0 += R.ntiles;
@@ -443,6 +446,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
         h->reps.push_back(R);
     }
     h->n_real = orig0;
+    h->capacity = std::max<long long>(orig0, capacity);
     View &V = h->V;
     V.n_pad = atom0;
     V.n_tiles = tile0;
@@ -542,7 +546,7 @@ static md_status create_impl(int n_rep, const md_config *cfgs, const double *con
     AL(V.scan_blk, (size_t)(V.nbins_total + 4095) / 4096 + 1);
     AL(V.rep_base, (size_t)n_rep);
     AL(V.ncount, n);
-    AL(V.inv, (size_t)h->n_real);
+    AL(V.inv, (size_t)h->capacity);
     {
         // tile tables sized for the smallest tile (32 atoms)
         const size_t nt = (n + 31) / 32;
@@ -685,6 +689,43 @@ md_status md_batch_create(int32_t n_rep, const md_config *cfgs, const double *co
                           const int32_t *const *type, md_system **out) {
     if (!cfgs || !x || !v || !type) return fail(nullptr, MD_ERR_INVALID, "null argument");
     return create_impl(n_rep, cfgs, x, v, type, out);
+}
+
+md_status md_create_capacity(const md_config *cfg, int64_t capacity, const double *x, const double *v,
+                             const int32_t *type, md_system **out) {
+    if (!cfg) return fail(nullptr, MD_ERR_INVALID, "null config");
+    if (capacity < cfg->n_atoms || capacity > (int64_t)kMaxAtoms)
+        return fail(nullptr, MD_ERR_INVALID, "capacity must be at least n_atoms and at most 2^26");
+    const double *xs[1] = {x};
+    const double *vs[1] = {v};
+    const int32_t *ts[1] = {type};
+    return create_impl(1, cfg, xs, vs, ts, out, capacity);
+}
+
+md_status md_reset(md_system *h, int64_t n, const double *x, const double *v, const int32_t *type) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "null handle");
+    if (h->n_rep != 1) return fail(h, MD_ERR_UNSUPPORTED, "md_reset: single-system handles only");
+    if (!x || !v || !type) return fail(h, MD_ERR_INVALID, "null argument");
+    if (n < 1) return fail(h, MD_ERR_INVALID, "md_reset: n must be positive");
+    if (n > h->capacity)
+        return fail(h, MD_ERR_UNSUPPORTED, "md_reset: %lld atoms exceed the handle's capacity %lld", (long long)n,
+                    (long long)h->capacity);
+    {
+        std::vector<int32_t> ht((size_t)n);
+        CK(h, cudaStreamSynchronize(h->s));
+        CK(h, cudaMemcpy(ht.data(), type, ht.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int32_t t : ht)
+            if (t < 0 || t >= h->cfg.n_types) return fail(h, MD_ERR_INVALID, "md_reset: atom type %d out of range", t);
+    }
+    Rep &R = h->reps[0];
+    R.natoms = (int)n;
+    h->n_real = n;
+    h->cfg.n_atoms = n;
+    CK(h, cudaMemcpyAsync((void *)h->V.rep, &R, sizeof(Rep), cudaMemcpyHostToDevice, h->s));
+    CK(h, launch_stage_in(h->V, 0, (int)n, x, v, type, h->s));
+    md_status st = full_rebuild(h, true);
+    if (st) return st;
+    return compute_forces(h, kModeStoreF);
 }
 
 md_status md_destroy(md_system *h) {

@@ -217,8 +217,9 @@ class SlabDomain:
 
     x, v: the owned atoms (global frame, host arrays); ids: their global
     indices; types: their types.  make_system(x, v, types, box, n_types,
-    params) builds the handle (default: a System with the potential settings
-    given here).  Collective: every rank constructs, steps and rebuilds
+    params, mass, capacity) builds the handle (default: a System with the
+    potential settings given here); the handle has spare atom capacity and is
+    kept across rebuilds (md_reset) while the sub-domain's atoms fit it.  Collective: every rank constructs, steps and rebuilds
     together.
     """
 
@@ -240,6 +241,8 @@ class SlabDomain:
         self.kw = dict(potential=potential, cutoff=cutoff, skin=skin, dt=dt, ftm2v=ftm2v,
                        energy_shift=energy_shift, precision=precision, list=list, tpa=tpa)
         self.make_system = make_system or self._default_system
+        self.slack = 0.1  # spare atom capacity of a handle, as a fraction of its first count
+        self.handles_made = 0
         self.s = None
         self.kernel = None  # force-kernel variant chosen for the first handle, kept afterwards
         self.rebuilds = 0
@@ -249,9 +252,9 @@ class SlabDomain:
         self._forces()
 
     # ------------------------------------------------------------ set-up --
-    def _default_system(self, x, v, types, box, n_types, params, mass):
+    def _default_system(self, x, v, types, box, n_types, params, mass, capacity):
         from .system import System
-        return System(x, v, types, box, params=params, n_types=n_types, mass=mass, **self.kw)
+        return System(x, v, types, box, params=params, n_types=n_types, mass=mass, capacity=capacity, **self.kw)
 
     def _local_params(self):
         """Parameters and masses of the handle's types (ghost types under newton)."""
@@ -290,9 +293,16 @@ class SlabDomain:
         vl = np.concatenate([v, np.zeros_like(got_lo["x"]), np.zeros_like(got_up["x"])])
         tl = np.concatenate([types, got_lo["t"] + gshift, got_up["t"] + gshift]).astype(np.int32)
         nt, params, mass = self._local_params()
-        if self.s is not None:
-            self.s.close()
-        self.s = self.make_system(xl, vl, tl, lay.local_box, nt, params, mass)
+        if self.s is not None and len(xl) <= self.s.capacity:
+            # the same handle, its device memory and graphs kept: new atoms only
+            self.s.reset(xl, vl, tl)
+        else:
+            if self.s is not None:
+                self.s.close()
+            # room for the atom count to drift between rebuilds (migration, ghost reselection)
+            cap = int(len(xl) * (1.0 + self.slack)) + 64
+            self.s = self.make_system(xl, vl, tl, lay.local_box, nt, params, mass, cap)
+            self.handles_made += 1
         if self.kernel is None:
             # the first handle's variant (chosen by its set-up benchmark when
             # tpa = 0) is kept for the handles of later rebuilds

@@ -59,7 +59,7 @@ class System:
     """
 
     def __init__(self, x, v, types, box, *, potential="lj", params, cutoff, skin, dt, mass, n_types=1,
-                 ftm2v=1.0, energy_shift=False, precision="mixed", list="full", tpa=1):
+                 ftm2v=1.0, energy_shift=False, precision="mixed", list="full", tpa=1, capacity=None):
         _require_cuda()
         self._lib = L.load()
         x = _dev(x, torch.float64, (-1, 3))
@@ -70,9 +70,14 @@ class System:
         cfg = self._config(n, box, potential, params, cutoff, skin, dt, mass, n_types, ftm2v, energy_shift,
                            precision, list, tpa)
         h = ctypes.c_void_p()
-        self._check(self._lib.md_create(ctypes.byref(cfg), _ptr(x), _ptr(v), _ptr(t), ctypes.byref(h)), None)
+        if capacity is None:
+            self._check(self._lib.md_create(ctypes.byref(cfg), _ptr(x), _ptr(v), _ptr(t), ctypes.byref(h)), None)
+        else:
+            self._check(self._lib.md_create_capacity(ctypes.byref(cfg), ctypes.c_int64(int(capacity)), _ptr(x),
+                                                     _ptr(v), _ptr(t), ctypes.byref(h)), None)
         self._h = h
         self._version = 0  # bumped whenever positions or parameters change
+        self.capacity = max(n, int(capacity or 0))
         self.n = n
         self.n_rep = 1
         self.n_types = n_types
@@ -210,6 +215,17 @@ class System:
         self._version += 1
         self._call("md_set_state", _ptr(xd), _ptr(vd))
         torch.cuda.current_stream().synchronize()
+
+    def reset(self, x, v, types=None):
+        """Replace every atom (n <= capacity): new positions, velocities and types,
+        same box, parameters, kernel variant and device memory."""
+        x = _dev(x, torch.float64, (-1, 3))
+        v = _dev(v, torch.float64, (-1, 3))
+        n = x.shape[0]
+        t = _dev(types if types is not None else np.zeros(n, np.int32), torch.int32, (n,))
+        self._version += 1
+        self._call("md_reset", ctypes.c_int64(n), _ptr(x), _ptr(v), _ptr(t))
+        self.n = n
 
     def set_params(self, params):
         p = np.ascontiguousarray(params, dtype=np.float64).ravel()

@@ -15,9 +15,10 @@ VV_DRIFT, VV_DISP, VV_DENSITY, VV_FORCE, VV_KICK = range(5)
 class OracleSystem:
     device = "cpu"
 
-    def __init__(self, x, v, types, box, n_types, params, mass, *, potential, cutoff, skin, dt, ftm2v=1.0,
-                 energy_shift=False, precision="fp64", list="full", tpa=1):
+    def __init__(self, x, v, types, box, n_types, params, mass, capacity=None, *, potential, cutoff, skin, dt,
+                 ftm2v=1.0, energy_shift=False, precision="fp64", list="full", tpa=1):
         assert potential == "lj"
+        self.capacity = max(len(x), int(capacity or 0))
         self.box = np.asarray(box, np.float64)
         self.x = np.mod(np.array(x, np.float64), self.box)
         self.v = np.array(v, np.float64)
@@ -26,7 +27,8 @@ class OracleSystem:
         p = np.asarray(params, np.float64)
         self.eps = p[:n_types * n_types].reshape(n_types, n_types)
         self.sig = p[n_types * n_types:].reshape(n_types, n_types)
-        self.m = np.asarray(mass, np.float64)[self.t][:, None]
+        self.mass_of_type = np.asarray(mass, np.float64)
+        self.m = self.mass_of_type[self.t][:, None]
         self.rc, self.dt, self.ftm2v = cutoff, dt, ftm2v
         self.list = list
         self.x_build = self.x.copy()
@@ -34,6 +36,15 @@ class OracleSystem:
 
     def _forces(self):
         return oracle.lj(self.x, self.box, self.rc, eps=self.eps, sig=self.sig, types=self.t, n_types=self.nt)[0]
+
+    def reset(self, x, v, types):
+        assert len(x) <= self.capacity
+        self.x = np.mod(np.array(x, np.float64), self.box)
+        self.v = np.array(v, np.float64)
+        self.t = np.asarray(types, np.int32)
+        self.m = self.mass_of_type[self.t][:, None]
+        self.x_build = self.x.copy()
+        self.f = self._forces()
 
     def info(self):
         return {"tpa": 1, "list": self.list, "block": 128, "vec": 1}

@@ -76,6 +76,7 @@ def _run_threads(P, x, v, box, nsteps, newton=False, lst="full"):
             f0 = d.owned_state()
             d.step(nsteps)
             out[r] = (f0, d.owned_state(), d.rebuilds)
+            assert d.handles_made == 1  # one handle, reset at every rebuild
         except Exception as e:  # surfaced in the main thread
             errors.append(e)
             world.barrier.abort()

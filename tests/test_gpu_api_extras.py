@@ -88,3 +88,39 @@ def test_ceiling_probes_are_sane():
     assert c["fp32_fma_tflops"] > 10 * c["fp64_fma_tflops"] > 0
     assert 1000 < c["hbm_copy_gbs"] < 20000
     assert c["l2_gather_gps"] > 10 and c["l2_gather_gbs"] == pytest.approx(16 * c["l2_gather_gps"])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_reset_within_capacity_equals_a_new_handle(prec, tol):
+    # one handle made with room for 1,000 more atoms, reset to a smaller, then a
+    # larger system: forces, energies and lists as a fresh handle's (stale data in
+    # slots that became padding must not leak into sums), and steps that follow
+    from paper_1009_4330_gb300 import MDError, System
+    from gpu_util import gpu_lists
+    a = lj_case(7, 0.08, seed=74)   # 1,372 atoms
+    c = lj_case(7, 0.10, seed=76)   # the same box
+    n_cap = a["x"].shape[0] + 1000
+    with System.lj(a["x"], a["v"], a["box"], cutoff=RC, skin=SKIN, dt=DT, mass=1.0, precision=prec, tpa=4,
+                   capacity=n_cap, energy_shift=False) as s:
+        assert s.capacity == n_cap
+        # a system of the same box with fewer atoms: drop the last 400 of case c
+        xs, vs = c["x"][:-400], c["v"][:-400]
+        s.energy_virial()  # fill the per-atom terms of all 1,372 slots
+        s.reset(xs, vs)
+        f, e, w = oracle.lj(xs, c["box"], RC)
+        assert rel_maxnorm(s.compute_forces().cpu().numpy(), f) < tol
+        ev = s.energy_virial().cpu().numpy()[0]
+        assert ev[0] == pytest.approx(e, rel=max(tol, 1e-7))
+        assert ev[1] == pytest.approx(oracle.kinetic(vs, [1.0]), rel=1e-12)
+        ref = oracle.neighbors(xs, c["box"], RC + SKIN)
+        got = gpu_lists(*s.neighbors())
+        assert all(np.array_equal(g, r) for g, r in zip(got, ref))
+        # back up to the full case c (more atoms than the handle held), then step
+        s.reset(c["x"], c["v"])
+        s.step(30)
+        x1 = s.state()[0].cpu().numpy()
+        refn = oracle.nve(c["x"], c["v"], c["box"], 30, DT, RC, SKIN)
+        assert np.abs(wrap_diff(x1, refn["x"], c["box"])).max() < (1e-9 if prec == "fp64" else 1e-5)
+        with pytest.raises(MDError, match="capacity"):
+            big = np.concatenate([c["x"]] * 2)
+            s.reset(big, np.zeros_like(big))

@@ -65,6 +65,7 @@ def run(P, x, v, box, nsteps, *, potential="lj", params=(1.0, 1.0), cutoff=RC, s
                 d.step(nsteps)
                 out["end"] = d.owned_state()
             out["rebuilds"] = d.rebuilds
+            out["handles"] = d.handles_made
             res[r] = out
             d.close()
         except Exception as e:
@@ -89,7 +90,8 @@ def run(P, x, v, box, nsteps, *, potential="lj", params=(1.0, 1.0), cutoff=RC, s
             ids, xx, vv, _ = o["end"]
             xe[ids], ve[ids] = xx, vv
         lists.update(o.get("lists", {}))
-    return dict(f0=f0, x=xe, v=ve, lists=lists, ev=res[0].get("ev"), rebuilds=[o["rebuilds"] for o in res])
+    return dict(f0=f0, x=xe, v=ve, lists=lists, ev=res[0].get("ev"), rebuilds=[o["rebuilds"] for o in res],
+                handles=[o["handles"] for o in res])
 
 
 @pytest.mark.parametrize("P", [2, 3])
@@ -108,6 +110,7 @@ def test_lj_full_lists_forces_energy_and_trajectory(P):
     assert np.abs(ev[2:] - w).max() <= 1e-12 * np.abs(w).max()
     ref = oracle.nve(x, v, box, 100, DT, RC, SKIN)
     assert min(out["rebuilds"]) >= 5
+    assert out["handles"] == [1] * P  # each slab's handle kept across its rebuilds (md_reset)
     assert np.abs(wrap_diff(out["x"], ref["x"], box)).max() < 1e-9
     assert np.abs(out["v"] - ref["v"]).max() < 1e-9
 
