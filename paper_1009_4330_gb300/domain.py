@@ -145,17 +145,6 @@ class TorchComm:
         self._pair(send, recv, dst, src)
         return recv.to(t.device)
 
-    def sendrecv_host(self, arrays, dst, src):
-        """Exchange a dict of numpy arrays with equal first dimension."""
-        out = {}
-        for k in sorted(arrays):
-            a = np.ascontiguousarray(arrays[k])
-            flat = torch.from_numpy(a.reshape(a.shape[0], -1).view(np.uint8).copy()) if a.size else \
-                torch.empty((a.shape[0], a.dtype.itemsize * int(np.prod(a.shape[1:]))), dtype=torch.uint8)
-            r = self.sendrecv(flat, dst, src)
-            out[k] = r.numpy().view(a.dtype).reshape((r.shape[0],) + a.shape[1:])
-        return out
-
     def allreduce_max(self, x):
         t = torch.tensor([float(x)], dtype=torch.float64)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
@@ -189,10 +178,6 @@ class ThreadComm:
 
     def sendrecv(self, t, dst, src):
         self.world.q[(self.rank, dst)].put(t)
-        return self.world.q[(src, self.rank)].get(timeout=self.world.timeout)
-
-    def sendrecv_host(self, arrays, dst, src):
-        self.world.q[(self.rank, dst)].put({k: np.array(v, copy=True) for k, v in arrays.items()})
         return self.world.q[(src, self.rank)].get(timeout=self.world.timeout)
 
     def _reduce(self, x, op):
@@ -248,7 +233,8 @@ class SlabDomain:
         self.rebuilds = 0
         xl = layout.to_local(x, self.r)
         t = np.zeros(len(xl), np.int32) if types is None else np.asarray(types, np.int32)
-        self._make_handle(xl, np.asarray(v, np.float64), np.asarray(ids, np.int64), t)
+        order = np.argsort(np.asarray(ids), kind="stable")  # first handle: owned atoms in global-id order
+        self._make_handle(xl[order], np.asarray(v, np.float64)[order], np.asarray(ids, np.int64)[order], t[order])
         self._forces()
 
     # ------------------------------------------------------------ set-up --
@@ -274,33 +260,47 @@ class SlabDomain:
     def _idx(self, a):
         return torch.as_tensor(np.asarray(a, dtype=np.int32), device=self.device)
 
+    def _xchg(self, rows, dst, src):
+        """Exchange a dict of tensors with equal first dimension (row sets)."""
+        return {k: self.comm.sendrecv(rows[k].contiguous(), dst, src) for k in sorted(rows)}
+
     def _make_handle(self, x, v, ids, types):
         """Choose and exchange the ghosts for owned atoms (x in this rank's
-        frame), then make the handle: owned, lower ghosts, upper ghosts."""
-        lay, comm = self.lay, self.comm
-        order = np.argsort(ids, kind="stable")  # owned atoms in global-id order (deterministic)
-        x, v, ids, types = x[order], v[order], ids[order], types[order]
-        up_rows, down_rows = lay.send_rows(x[:, lay.axis])
+        frame; tensors on this rank's device, or host arrays), then make or
+        reset the handle: owned, lower ghosts, upper ghosts.  Row selection
+        and concatenation stay on the device; only the rows that cross to a
+        neighbour are handed over."""
+        lay, dev = self.lay, self.device
+        x = torch.as_tensor(x, dtype=torch.float64, device=dev)
+        v = torch.as_tensor(v, dtype=torch.float64, device=dev)
+        ids = torch.as_tensor(ids, dtype=torch.int64, device=dev)
+        types = torch.as_tensor(types, dtype=torch.int32, device=dev)
+        z = x[:, lay.axis]
+        up_rows = torch.nonzero(z >= lay.off + lay.Ls - lay.rl).flatten()
+        down_rows = torch.nonzero(z < lay.off + lay.rl).flatten()
         if self.newton:
             up_rows = up_rows[:0]  # ghosts only from the slab above
-        sh_up, sh_down = lay.shift(-1.0), lay.shift(+1.0)
-        got_lo = comm.sendrecv_host({"x": x[up_rows] + sh_up, "t": types[up_rows], "i": ids[up_rows]},
-                                    lay.up(self.r), lay.down(self.r))
-        got_up = comm.sendrecv_host({"x": x[down_rows] + sh_down, "t": types[down_rows], "i": ids[down_rows]},
-                                    lay.down(self.r), lay.up(self.r))
+        sh_up = torch.as_tensor(lay.shift(-1.0), device=dev)
+        sh_down = torch.as_tensor(lay.shift(+1.0), device=dev)
+        got_lo = self._xchg({"x": x[up_rows] + sh_up, "t": types[up_rows], "i": ids[up_rows]},
+                            lay.up(self.r), lay.down(self.r))
+        got_up = self._xchg({"x": x[down_rows] + sh_down, "t": types[down_rows], "i": ids[down_rows]},
+                            lay.down(self.r), lay.up(self.r))
         gshift = self.nt if self.newton else 0
-        xl = np.concatenate([x, got_lo["x"], got_up["x"]])
-        vl = np.concatenate([v, np.zeros_like(got_lo["x"]), np.zeros_like(got_up["x"])])
-        tl = np.concatenate([types, got_lo["t"] + gshift, got_up["t"] + gshift]).astype(np.int32)
+        xl = torch.cat([x, got_lo["x"], got_up["x"]])
+        vl = torch.cat([v, torch.zeros_like(got_lo["x"]), torch.zeros_like(got_up["x"])])
+        tl = torch.cat([types, got_lo["t"] + gshift, got_up["t"] + gshift]).to(torch.int32)
         nt, params, mass = self._local_params()
-        if self.s is not None and len(xl) <= self.s.capacity:
+        made = False
+        if self.s is not None and xl.shape[0] <= self.s.capacity:
             # the same handle, its device memory and graphs kept: new atoms only
             self.s.reset(xl, vl, tl)
         else:
+            made = True
             if self.s is not None:
                 self.s.close()
             # room for the atom count to drift between rebuilds (migration, ghost reselection)
-            cap = int(len(xl) * (1.0 + self.slack)) + 64
+            cap = int(xl.shape[0] * (1.0 + self.slack)) + 64
             self.s = self.make_system(xl, vl, tl, lay.local_box, nt, params, mass, cap)
             self.handles_made += 1
         if self.kernel is None:
@@ -309,20 +309,26 @@ class SlabDomain:
             inf = self.s.info()
             self.kernel = (inf["tpa"], inf["list"], inf["block"], inf["vec"])
             self.kw["tpa"], self.kw["list"] = inf["tpa"], inf["list"]
-        else:
+        elif made:
             inf = self.s.info()
             if (inf["tpa"], inf["list"], inf["block"], inf["vec"]) != self.kernel:
                 self.s.set_kernel(*self.kernel)
-        self.ids, self.types = ids, types
-        self.ghost_ids = np.concatenate([got_lo["i"], got_up["i"]]).astype(np.int64)
-        self.n_own = len(ids)
-        n_lo, n_up = len(got_lo["x"]), len(got_up["x"])
-        self.send_up = self._idx(up_rows)
-        self.send_down = self._idx(down_rows)
-        self.lo = self._idx(np.arange(self.n_own, self.n_own + n_lo))
-        self.up = self._idx(np.arange(self.n_own + n_lo, self.n_own + n_lo + n_up))
-        self.owned = self._idx(np.arange(self.n_own))
-        self.all_local = self._idx(np.arange(self.n_own + n_lo + n_up))
+        self.ids_d, self.types_d = ids, types
+        self.ghost_ids_d = torch.cat([got_lo["i"], got_up["i"]])
+        self.n_own = int(ids.shape[0])
+        n_lo, n_up = int(got_lo["x"].shape[0]), int(got_up["x"].shape[0])
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.send_up = up_rows.to(torch.int32)
+        self.send_down = down_rows.to(torch.int32)
+        self.lo = torch.arange(self.n_own, self.n_own + n_lo, **i32)
+        self.up = torch.arange(self.n_own + n_lo, self.n_own + n_lo + n_up, **i32)
+        self.owned = torch.arange(self.n_own, **i32)
+        self.all_local = torch.arange(self.n_own + n_lo + n_up, **i32)
+
+    @property
+    def ids(self):
+        """Global indices of the owned atoms (host array), in the handle's order."""
+        return self.ids_d.cpu().numpy()
 
     # ------------------------------------------------------------ exchange --
     def _forward(self, what):
@@ -352,23 +358,27 @@ class SlabDomain:
             self._reverse_forces()
 
     def _rebuild(self):
-        """Migration of atoms that left the slab, new ghosts, new handle."""
-        lay, comm = self.lay, self.comm
+        """Migration of atoms that left the slab, new ghosts, the handle reset
+        (on the device; only the migrating and ghost rows are handed over)."""
+        lay = self.lay
         x, v, _ = self.s.state()
-        x = x[:self.n_own].cpu().numpy()
-        v = v[:self.n_own].cpu().numpy()
+        n = self.n_own
+        x, v = x[:n], v[:n]
         z = x[:, lay.axis]
-        go_down, go_up = lay.leaving(z)
+        go_down = z < lay.off
+        go_up = z >= lay.off + lay.Ls
         stay = ~(go_down | go_up)
-        xu, xd = x[go_up] + lay.shift(-1.0), x[go_down] + lay.shift(+1.0)
-        from_down = comm.sendrecv_host({"x": xu, "v": v[go_up], "i": self.ids[go_up], "t": self.types[go_up]},
-                                       lay.up(self.r), lay.down(self.r))
-        from_up = comm.sendrecv_host({"x": xd, "v": v[go_down], "i": self.ids[go_down], "t": self.types[go_down]},
-                                     lay.down(self.r), lay.up(self.r))
-        xn = np.concatenate([x[stay], from_down["x"], from_up["x"]])
-        vn = np.concatenate([v[stay], from_down["v"], from_up["v"]])
-        ids = np.concatenate([self.ids[stay], from_down["i"], from_up["i"]])
-        ts = np.concatenate([self.types[stay], from_down["t"], from_up["t"]])
+        dev = self.device
+        sh_up = torch.as_tensor(lay.shift(-1.0), device=dev)
+        sh_down = torch.as_tensor(lay.shift(+1.0), device=dev)
+        from_down = self._xchg({"x": x[go_up] + sh_up, "v": v[go_up], "i": self.ids_d[go_up],
+                                "t": self.types_d[go_up]}, lay.up(self.r), lay.down(self.r))
+        from_up = self._xchg({"x": x[go_down] + sh_down, "v": v[go_down], "i": self.ids_d[go_down],
+                              "t": self.types_d[go_down]}, lay.down(self.r), lay.up(self.r))
+        xn = torch.cat([x[stay], from_down["x"], from_up["x"]])
+        vn = torch.cat([v[stay], from_down["v"], from_up["v"]])
+        ids = torch.cat([self.ids_d[stay], from_down["i"], from_up["i"]])
+        ts = torch.cat([self.types_d[stay], from_down["t"], from_up["t"]])
         self._make_handle(xn, vn, ids, ts)
         self.rebuilds += 1
 
@@ -389,12 +399,12 @@ class SlabDomain:
         """(ids, x global frame, v, f) of the atoms this rank owns (host arrays)."""
         x, v, f = self.s.state()
         n = self.n_own
-        return (self.ids.copy(), self.lay.to_global(x[:n].cpu().numpy(), self.r), v[:n].cpu().numpy(),
+        return (self.ids, self.lay.to_global(x[:n].cpu().numpy(), self.r), v[:n].cpu().numpy(),
                 f[:n].cpu().numpy())
 
     def local_to_global(self):
         """Global index of every atom of the handle (owned, then ghosts), in its original order."""
-        return np.concatenate([self.ids, self.ghost_ids])
+        return torch.cat([self.ids_d, self.ghost_ids_d]).cpu().numpy()
 
     def energies(self):
         """Global (Epot, Ekin, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz), summed over ranks;

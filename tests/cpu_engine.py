@@ -12,6 +12,13 @@ HALO_X, HALO_V, HALO_F = 1, 2, 4
 VV_DRIFT, VV_DISP, VV_DENSITY, VV_FORCE, VV_KICK = range(5)
 
 
+def _np(a, dtype):
+    """a host copy of an array or CPU tensor"""
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.array(a, dtype=dtype, copy=True)
+
+
 class OracleSystem:
     device = "cpu"
 
@@ -20,9 +27,9 @@ class OracleSystem:
         assert potential == "lj"
         self.capacity = max(len(x), int(capacity or 0))
         self.box = np.asarray(box, np.float64)
-        self.x = np.mod(np.array(x, np.float64), self.box)
-        self.v = np.array(v, np.float64)
-        self.t = np.asarray(types, np.int32)
+        self.x = np.mod(_np(x, np.float64), self.box)
+        self.v = _np(v, np.float64)
+        self.t = _np(types, np.int32)
         self.nt = n_types
         p = np.asarray(params, np.float64)
         self.eps = p[:n_types * n_types].reshape(n_types, n_types)
@@ -39,9 +46,9 @@ class OracleSystem:
 
     def reset(self, x, v, types):
         assert len(x) <= self.capacity
-        self.x = np.mod(np.array(x, np.float64), self.box)
-        self.v = np.array(v, np.float64)
-        self.t = np.asarray(types, np.int32)
+        self.x = np.mod(_np(x, np.float64), self.box)
+        self.v = _np(v, np.float64)
+        self.t = _np(types, np.int32)
         self.m = self.mass_of_type[self.t][:, None]
         self.x_build = self.x.copy()
         self.f = self._forces()
