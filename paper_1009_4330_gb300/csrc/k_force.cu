@@ -205,7 +205,7 @@ __device__ __forceinline__ void epilogue(const View &V, int mode, int rem, int p
                                          double fz, const double *s_ftm) {
     const int n = V.n_pad;
     if (mode == kModeStep || mode == kModeKickDry) {
-        const bool last = (mode == kModeStep && rem == 1);
+        const bool last = (mode == kModeStep && rem == 0);
         const double c = (mode == kModeKickDry) ? 0.0 : (last ? 0.5 : 1.0) * V.dt * s_ftm[t];
         V.v[p] += c * fx;
         V.v[n + p] += c * fy;
@@ -224,23 +224,6 @@ __device__ __forceinline__ void write_ev(const View &V, int p, int t, double e, 
     V.ev[p] = e;
     V.ev[n + p] = 0.5 * (vx * vx + vy * vy + vz * vz) / s_ftm[t];
     for (int k = 0; k < 6; ++k) V.ev[(2 + k) * n + p] = w[k];
-}
-
-// md_step bookkeeping by the last block of the step's final kernel
-__device__ __forceinline__ void finish_step(const View &V, const KArgs &a) {
-    if (a.mode != kModeStep) return;
-    if (last_block(&V.ctl->ticket_force)) {
-        if (threadIdx.x == 0) {
-            V.ctl->ticket_force = 0;
-            // a latched error made this pass skip its work: the step is not done
-            // (the host finishes it after recovering from a list overflow)
-            const bool done = V.ctl->err == 0;
-            const int rem = V.ctl->remaining - (done ? 1 : 0);
-            V.ctl->remaining = rem;
-            if (done) V.ctl->steps += 1;
-            if (a.in_graph) cudaGraphSetConditional(V.cond_loop, (rem > 0 && done) ? 1u : 0u);
-        }
-    }
 }
 
 // ---------------------------------------------------------------- LJ ----
@@ -494,7 +477,6 @@ __global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, 
             if (EV) write_ev(V, p, pr.ti, e_acc, w_acc, s_ftm);
         }
     }
-    if (!HALF) finish_step(V, a);
 }
 
 // Cell-list force pass, no Verlet list (the alternative the paper measures
@@ -586,7 +568,6 @@ __global__ void __launch_bounds__(128) k_lj_cells(View V, KArgs a) {
         }
     }
     if (valid) epilogue(V, a.mode, rem, p, pr.ti, pr.ax.value(), pr.ay.value(), pr.az.value(), s_ftm);
-    finish_step(V, a);
 }
 
 void cells_force_sequence(const View &V, int mode, std::vector<KCall> &seq) {
@@ -686,7 +667,7 @@ __global__ void k_kick(View V, KArgs a) {
             const int t = V.type[p];
             if (a.mode == kModeStep || a.mode == kModeKickDry || a.mode == kModeHalfKick) {
                 const double c = (a.mode == kModeKickDry) ? 0.0
-                                 : (a.mode == kModeHalfKick || rem == 1 ? 0.5 : 1.0) * V.dt * s_ftm[t];
+                                 : (a.mode == kModeHalfKick || rem == 0 ? 0.5 : 1.0) * V.dt * s_ftm[t];
                 V.v[p] += c * V.f[p];
                 V.v[n + p] += c * V.f[n + p];
                 V.v[2 * n + p] += c * V.f[2 * n + p];
@@ -696,7 +677,6 @@ __global__ void k_kick(View V, KArgs a) {
             }
         }
     }
-    finish_step(V, a);
 }
 
 // --------------------------------------------------------------- EAM ----
@@ -874,7 +854,6 @@ __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
         epilogue(V, a.mode, rem, p, 0, fx, fy, fz, s_ftm);
         if (EV) write_ev(V, p, 0, e_acc + V.emb[p], w_acc, s_ftm);
     }
-    finish_step(V, a);
 }
 
 // ------------------------------------------------------- drift + control --
@@ -1008,6 +987,19 @@ __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
 #pragma unroll
     for (int u = 0; u < kDriftPer; ++u) note_disp(V.rep_disp, V.skin_half2f, d2[u], rep[u]);
     if (last_block(&V.ctl->ticket_drift)) {
+        if (err != 0) {
+            // a latched error: this drift changed nothing (the loop iteration
+            // after a step whose rebuild overflowed); the rebuild flags stay as
+            // that step's drift set them, for the host's recovery
+            if (threadIdx.x == 0) {
+                V.ctl->ticket_drift = 0;
+                if (a.in_graph) {
+                    cudaGraphSetConditional(V.cond_rebuild, 0u);
+                    cudaGraphSetConditional(V.cond_loop, 0u);
+                }
+            }
+            return;
+        }
         int any = 0;
         bool bad = false;
         for (int q = threadIdx.x; q < V.n_rep; q += blockDim.x) {
@@ -1024,7 +1016,24 @@ __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
         if (threadIdx.x == 0) {
             V.ctl->ticket_drift = 0;
             V.ctl->first = 0;
-            if (a.in_graph) cudaGraphSetConditional(V.cond_rebuild, (any && V.ctl->err == 0) ? 1u : 0u);
+            // The step's bookkeeping, here rather than at the end of the force
+            // pass (whose every block would otherwise take a ticket): a step
+            // whose drift left the state sound counts, and the force pass of
+            // this step finds the remaining count already decremented (0 on
+            // the last step: the closing half kick).  If this step's rebuild
+            // then overflows the list, its force pass skips, the next drift
+            // sees the latched error and ends the loop without counting, and
+            // the host completes the step after growing the list.
+            const bool ok = V.ctl->err == 0;
+            int rem = V.ctl->remaining;
+            if (ok) {
+                V.ctl->steps += 1;
+                if (rem > 0) V.ctl->remaining = --rem;
+            }
+            if (a.in_graph) {
+                cudaGraphSetConditional(V.cond_rebuild, (any && ok) ? 1u : 0u);
+                cudaGraphSetConditional(V.cond_loop, (rem > 0 && ok) ? 1u : 0u);
+            }
         }
     }
 }

@@ -12,8 +12,8 @@
 //   }
 //
 // k_drift's last block sets cond_rebuild from the per-replica displacement
-// check; the force pass's last block decrements the remaining step count and
-// sets cond_loop.  No host round trip per step.
+// check, counts the step, decrements the remaining step count and sets
+// cond_loop; the force pass takes no ticket.  No host round trip per step.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

@@ -67,10 +67,9 @@ struct Rep {                // one replica (periodic box), device-resident
 
 struct Ctl {                // device control block of a handle
     unsigned err;           // latched kErr* bits
-    int remaining;          // steps left in the running md_step
+    int remaining;          // steps left in the running md_step (decremented by each step's drift)
     int first;              // 1: the next drift applies the half kick from the stored F
     unsigned ticket_drift;  // last-block tickets (reset by the last block)
-    unsigned ticket_force;
     unsigned ticket_build;
     int need_maxneigh;      // largest list length seen by an overflowing build
     long long steps;        // completed time steps
