@@ -957,6 +957,7 @@ template <int PREC>
 __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
     const unsigned err = V.ctl->err;
     const int first = V.ctl->first;
+    if (blockIdx.x == 0 && threadIdx.x == 0) V.ctl->err_at_drift = err;  // for k_drift_done
     float d2[kDriftPer];
     int rep[kDriftPer];
     if constexpr (PREC == MD_PREC_MIXED) {
@@ -986,54 +987,58 @@ __global__ void __launch_bounds__(256) k_drift(View V, KArgs a) {
     }
 #pragma unroll
     for (int u = 0; u < kDriftPer; ++u) note_disp(V.rep_disp, V.skin_half2f, d2[u], rep[u]);
-    if (last_block(&V.ctl->ticket_drift)) {
-        if (err != 0) {
-            // a latched error: this drift changed nothing (the loop iteration
-            // after a step whose rebuild overflowed); the rebuild flags stay as
-            // that step's drift set them, for the host's recovery
-            if (threadIdx.x == 0) {
-                V.ctl->ticket_drift = 0;
-                if (a.in_graph) {
-                    cudaGraphSetConditional(V.cond_rebuild, 0u);
-                    cudaGraphSetConditional(V.cond_loop, 0u);
-                }
-            }
-            return;
+}
+
+// The step's bookkeeping after the drift, one block: the per-replica maximum
+// displacement becomes the rebuild flags (and the count of replica rebuilds),
+// the step is counted, the remaining count decremented and the graph's
+// conditionals set.  A separate kernel rather than the drift's last block:
+// the drift then takes no ticket (a fence and an atomic in each of its
+// blocks).  The force pass of the step finds the remaining count already
+// decremented (0 on the last step: the closing half kick).  If this step's
+// rebuild overflows the list, its force pass skips, the next iteration's
+// drift and this kernel see the latched error, change nothing (the rebuild
+// flags stay for the host's recovery) and end the loop, and the host
+// completes the step after growing the list.
+__global__ void __launch_bounds__(256) k_drift_done(View V, KArgs a) {
+    if (V.ctl->err_at_drift != 0) {
+        if (threadIdx.x == 0 && a.in_graph) {
+            cudaGraphSetConditional(V.cond_rebuild, 0u);
+            cudaGraphSetConditional(V.cond_loop, 0u);
         }
-        int any = 0;
-        bool bad = false;
-        for (int q = threadIdx.x; q < V.n_rep; q += blockDim.x) {
-            const unsigned m = V.rep_disp[q];
-            V.rep_disp[q] = 0u;
-            const bool nonfin = m >= 0x7f800000u;
-            const int flag = (nonfin || __uint_as_float(m) > V.skin_half2f) ? 1 : 0;
-            V.rep_flag[q] = flag;
-            any |= flag;
-            bad |= nonfin;
+        return;
+    }
+    int any = 0, nflag = 0;
+    bool bad = false;
+    for (int q = threadIdx.x; q < V.n_rep; q += blockDim.x) {
+        const unsigned m = V.rep_disp[q];
+        V.rep_disp[q] = 0u;
+        const bool nonfin = m >= 0x7f800000u;
+        const int flag = (nonfin || __uint_as_float(m) > V.skin_half2f) ? 1 : 0;
+        V.rep_flag[q] = flag;
+        any |= flag;
+        nflag += flag;
+        bad |= nonfin;
+    }
+    if (bad) latch_error(V.ctl, kErrNonfinite);
+    __shared__ int s_n[8];
+    for (int o = 16; o > 0; o >>= 1) nflag += __shfl_xor_sync(0xffffffffu, nflag, o);
+    if ((threadIdx.x & 31) == 0) s_n[threadIdx.x >> 5] = nflag;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_n[k];
+        V.ctl->first = 0;
+        const bool ok = V.ctl->err == 0;
+        int rem = V.ctl->remaining;
+        if (ok) {
+            V.ctl->steps += 1;
+            V.ctl->rebuilds += tot;  // the builds this step's rebuild conditional runs
+            if (rem > 0) V.ctl->remaining = --rem;
         }
-        if (bad) latch_error(V.ctl, kErrNonfinite);
-        any = __syncthreads_or(any);
-        if (threadIdx.x == 0) {
-            V.ctl->ticket_drift = 0;
-            V.ctl->first = 0;
-            // The step's bookkeeping, here rather than at the end of the force
-            // pass (whose every block would otherwise take a ticket): a step
-            // whose drift left the state sound counts, and the force pass of
-            // this step finds the remaining count already decremented (0 on
-            // the last step: the closing half kick).  If this step's rebuild
-            // then overflows the list, its force pass skips, the next drift
-            // sees the latched error and ends the loop without counting, and
-            // the host completes the step after growing the list.
-            const bool ok = V.ctl->err == 0;
-            int rem = V.ctl->remaining;
-            if (ok) {
-                V.ctl->steps += 1;
-                if (rem > 0) V.ctl->remaining = --rem;
-            }
-            if (a.in_graph) {
-                cudaGraphSetConditional(V.cond_rebuild, (any && ok) ? 1u : 0u);
-                cudaGraphSetConditional(V.cond_loop, (rem > 0 && ok) ? 1u : 0u);
-            }
+        if (a.in_graph) {
+            cudaGraphSetConditional(V.cond_rebuild, (any && ok) ? 1u : 0u);
+            cudaGraphSetConditional(V.cond_loop, (rem > 0 && ok) ? 1u : 0u);
         }
     }
 }
@@ -1155,6 +1160,7 @@ void drift_sequence(const View &V, bool in_graph, std::vector<KCall> &seq) {
                             dim3((V.n_pad + 256 * kDriftPer - 1) / (256 * kDriftPer)), dim3(256), 0, a});
     else  // two atoms per thread
         seq.push_back(KCall{(const void *)k_drift<MD_PREC_MIXED>, dim3((V.n_pad / 2 + 255) / 256), dim3(256), 0, a});
+    seq.push_back(KCall{(const void *)k_drift_done, dim3(1), dim3(256), 0, a});
 }
 
 void kick_sequence(const View &V, int mode, std::vector<KCall> &seq) {

@@ -811,12 +811,13 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(Vi
             ss += s_sum[k];
         }
     }
-    if (last_block(&V.ctl->ticket_build)) {
+    // builds of every replica (creation, md_build_neighbors, md_set_state) are
+    // counted here; the step's builds of flagged replicas were counted with the
+    // flags (k_drift_done), so that those launches take no ticket
+    if (a.all && last_block(&V.ctl->ticket_build)) {
         if (threadIdx.x == 0) {
             V.ctl->ticket_build = 0;
-            int nr = 0;
-            for (int q = 0; q < V.n_rep; ++q) nr += (a.all || V.rep_flag[q]) ? 1 : 0;
-            V.ctl->rebuilds += nr;
+            V.ctl->rebuilds += V.n_rep;
         }
     }
 }
@@ -884,12 +885,6 @@ __global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build_wl
             const int r = V.bin_rep[gb];
             atomicMax(&V.rep_maxcnt[r], my_max);
             atomicAdd(&V.rep_entries[r], (unsigned long long)my_sum);
-        }
-    }
-    if (last_block(&V.ctl->ticket_build)) {
-        if (threadIdx.x == 0) {
-            V.ctl->ticket_build = 0;
-            V.ctl->rebuilds += nf;
         }
     }
 }

@@ -69,8 +69,8 @@ struct Ctl {                // device control block of a handle
     unsigned err;           // latched kErr* bits
     int remaining;          // steps left in the running md_step (decremented by each step's drift)
     int first;              // 1: the next drift applies the half kick from the stored F
-    unsigned ticket_drift;  // last-block tickets (reset by the last block)
-    unsigned ticket_build;
+    unsigned ticket_build;  // last-block ticket of the list build (reset by the last block)
+    unsigned err_at_drift;  // the error word as the step's drift found it (k_drift_done)
     int need_maxneigh;      // largest list length seen by an overflowing build
     long long steps;        // completed time steps
     long long rebuilds;     // completed replica builds
