@@ -443,9 +443,10 @@ def run_ours(args, ws, rank, local):
     ms = max_over_ranks(dist, ms)
     value = ws * n * K / (ms / 1000.0)
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
-    # our kernels in the timed region: loop control once, per step the drift and
-    # the force pass (1 kernel full list, 3 half list), 8 per list rebuild
-    launches = 1 + K * (1 + (3 if i1["list"] == "half" else 1)) + (9 if i1["tile_atoms"] else 8) * rebuilds
+    # our kernels in the timed region: loop control once; per step the drift,
+    # its one-block bookkeeping kernel and the force pass (1 kernel with a full
+    # list, 3 with a half list); 8 per list rebuild (9 with staged tiles)
+    launches = 1 + K * (2 + (3 if i1["list"] == "half" else 1)) + (9 if i1["tile_atoms"] else 8) * rebuilds
     # dominant kernel: the force pass as md_step runs it, timed with CUDA events on the handle's stream
     f_ms, f_bytes = s.time_force(warmup=3, reps=20)
     info = s.info()
