@@ -354,7 +354,8 @@ __device__ __forceinline__ void fix_near_warp(const View &V, LJPair<MD_PREC_MIXE
             const int tp = MT ? ti * pr.nt + tj : 0;
             const float r2i = Pol<MD_PREC_MIXED>::rcp(r2);
             const float r6i = r2i * r2i * r2i;
-            const float fpair = sgn * r6i * (pr.lj1[tp] * r6i - pr.lj2[tp]) * r2i;
+            const float a1 = MT ? pr.lj1[tp] : pr.c1, a2 = MT ? pr.lj2[tp] : pr.c2;
+            const float fpair = sgn * r6i * (a1 * r6i - a2) * r2i;
             const float fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
             cx += fxp; cy += fyp; cz += fzp;
             if (HALF) {
