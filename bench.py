@@ -445,8 +445,8 @@ def run_ours(args, ws, rank, local):
     rebuilds = i1["rebuilds"] - i0["rebuilds"]
     # our kernels in the timed region: loop control once; per step the drift,
     # its one-block bookkeeping kernel and the force pass (1 kernel with a full
-    # list, 3 with a half list); 8 per list rebuild (9 with staged tiles)
-    launches = 1 + K * (2 + (3 if i1["list"] == "half" else 1)) + (9 if i1["tile_atoms"] else 8) * rebuilds
+    # list, 3 with a half list); 7 per list rebuild (8 with staged tiles)
+    launches = 1 + K * (2 + (3 if i1["list"] == "half" else 1)) + (8 if i1["tile_atoms"] else 7) * rebuilds
     # dominant kernel: the force pass as md_step runs it, timed with CUDA events on the handle's stream
     f_ms, f_bytes = s.time_force(warmup=3, reps=20)
     info = s.info()

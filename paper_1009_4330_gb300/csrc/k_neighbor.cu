@@ -13,14 +13,15 @@
 
 namespace md {
 
-// Zero the bin counts and list statistics of each rebuilding replica (one
-// block per replica).
+// Zero the bin counts and list statistics of each rebuilding replica (a
+// grid-stride loop over all bins and replicas).
 __global__ void k_zero_bins(View V, KArgs a) {
-    const int r = blockIdx.x;
-    if (!a.all && !V.rep_flag[r]) return;
-    const int b0 = V.rep[r].bin0, nb = V.rep[r].nbins;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) V.bin_count[b0 + i] = 0;
-    if (threadIdx.x == 0) {
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int b = t0; b < V.nbins_total; b += stride)
+        if (a.all || V.rep_flag[V.bin_rep[b]]) V.bin_count[b] = 0;
+    for (int r = t0; r < V.n_rep; r += stride) {
+        if (!a.all && !V.rep_flag[r]) continue;
         V.rep_maxcnt[r] = 0;
         V.rep_entries[r] = 0ull;
     }
@@ -143,7 +144,7 @@ __global__ void k_prepare(View V, KArgs a) {
 // gathers of the force loop then hit L1 more often.
 
 // bin_start[b] = first slot of bin b: an exclusive scan of the bin counts,
-// segmented per replica (each replica's slots start at its atom0), in three
+// segmented per replica (each replica's slots start at its atom0), in two
 // parallel passes.  Bins of replicas that are not rebuilding get meaningless
 // values, which nothing reads before their next rebuild.
 constexpr int kScanBlock = 4096;  // bins per block of k_scan1 (1024 threads x 4)
@@ -173,8 +174,10 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
     return r;
 }
 
-// pass 1: prefix inside each block of 4096 bins, and the block totals
-__global__ void k_scan1(View V, KArgs a) {
+// pass 1: prefix inside each block of 4096 bins and the block totals; the
+// last block to finish (ticket) then scans the block totals and sets each
+// replica's base
+__global__ void __launch_bounds__(1024) k_scan1(View V, KArgs a) {
     __shared__ int s_warp[32];
     const int b0 = blockIdx.x * kScanBlock + threadIdx.x * 4;
     int c[4], sum = 0;
@@ -189,26 +192,24 @@ __global__ void k_scan1(View V, KArgs a) {
         run += c[k];
     }
     if (threadIdx.x == 0) V.scan_blk[blockIdx.x] = total;
-}
-
-// pass 2 (one block): exclusive scan of the block totals; per-replica bases
-__global__ void k_scan2(View V, KArgs a) {
-    __shared__ int s_warp[32];
-    const int nblk = (V.nbins_total + kScanBlock - 1) / kScanBlock;
+    if (!last_block(&V.ctl->ticket_scan)) return;
+    __threadfence();
+    const int nblk = gridDim.x;
     int carry = 0;
     for (int c0 = 0; c0 < nblk; c0 += blockDim.x) {
         const int i = c0 + threadIdx.x;
-        const int v = i < nblk ? V.scan_blk[i] : 0;
-        int total;
-        const int ex = block_excl_scan(v, s_warp, &total);
+        const int v = i < nblk ? __ldcg(&V.scan_blk[i]) : 0;
+        int tot;
+        const int ex = block_excl_scan(v, s_warp, &tot);
         if (i < nblk) V.scan_blk[i] = carry + ex;
-        carry += total;
+        carry += tot;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < V.n_rep; r += blockDim.x) {
         const int b = V.rep[r].bin0;
-        V.rep_base[r] = V.scan_blk[b / kScanBlock] + V.bin_start[b] - V.rep[r].atom0;
+        V.rep_base[r] = V.scan_blk[b / kScanBlock] + __ldcg(&V.bin_start[b]) - V.rep[r].atom0;
     }
+    if (threadIdx.x == 0) V.ctl->ticket_scan = 0;
 }
 
 // pass 3: global prefix, rebased to each rebuilding replica's first slot
@@ -501,6 +502,9 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
 constexpr int kBatch = 14;  // rounds whose list entries are appended together
 constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
+// blocks per SM the list build is compiled for: 7 (72 registers, 28 warps)
+// measured faster than 8 (64 registers, more spills) on the 864,000-atom liquid
+constexpr int kBuildBlocksPerSM = 7;
 
 template <int PREC, int HALF>
 __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int hsplit, int lane, int w,
@@ -609,38 +613,35 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
         unsigned nz = 0u;  // this home atom: rounds of the batch in which it accepts a candidate
         auto append = [&]() {
             __syncwarp();
-            int r = nz ? __ffs(nz) - 1 : rb;
-            unsigned t = r < rb ? s_t[w][r][lane] : 0u;
-            while (__any_sync(0xffffffffu, r < rb)) {
-                if (r < rb) {
-                    const uint32_t *row = &s_e[w][r][0];
-                    const int c1 = __ffs(t) - 1;
-                    t &= t - 1u;
-                    uint32_t e1 = row[c1];
-                    const bool two = t != 0u;  // a second entry from the same round
-                    uint32_t e2 = 0u;
-                    if (two) {
-                        e2 = row[__ffs(t) - 1];
-                        t &= t - 1u;
-                    }
-                    if (tpa_atoms) {
-                        e1 += (uint32_t)s_delta[w][tsel][e1 & 63u];
-                        e2 += (uint32_t)s_delta[w][tsel][e2 & 63u];
-                    }
-                    if (mycnt < maxn) lbase[slot] = e1;
-                    ++mycnt;
-                    slot += (mycnt & (tq - 1)) ? 1 : jump;
-                    if (two) {
-                        if (mycnt < maxn) lbase[slot] = e2;
-                        ++mycnt;
-                        slot += (mycnt & (tq - 1)) ? 1 : jump;
-                    }
-                    if (t == 0u) {  // next round with an accepted candidate
-                        const unsigned rest = nz & ~((2u << r) - 1u);
-                        r = rest ? __ffs(rest) - 1 : rb;
-                        if (r < rb) t = s_t[w][r][lane];
-                    }
+            // written without branches: every lane runs every iteration, a
+            // lane whose share is done with all its predicates false
+            int r = nz ? __ffs(nz) - 1 : 0;     // round being appended
+            unsigned t = nz ? s_t[w][r][lane] : 0u;  // its candidates not yet appended
+            unsigned rest = nz & (nz - 1u);      // later rounds with entries
+            while (__any_sync(0xffffffffu, t != 0u)) {
+                // up to two entries of round r
+                const unsigned t1 = t & (t - 1u), t2 = t1 & (t1 - 1u);
+                const int c1 = (__ffs(t) - 1) & 31, c2 = (__ffs(t1) - 1) & 31;
+                uint32_t e1 = s_e[w][r][c1], e2 = s_e[w][r][c2];
+                if (tpa_atoms) {
+                    e1 += (uint32_t)s_delta[w][tsel][e1 & 63u];
+                    e2 += (uint32_t)s_delta[w][tsel][e2 & 63u];
                 }
+                const bool s1 = t != 0u, s2 = t1 != 0u;
+                const int m1 = mycnt + 1, m2 = mycnt + 2;
+                const unsigned slot1 = slot + ((m1 & (tq - 1)) ? 1u : (unsigned)jump);
+                const unsigned slot2 = slot1 + ((m2 & (tq - 1)) ? 1u : (unsigned)jump);
+                if (s1 && mycnt < maxn) lbase[slot] = e1;
+                if (s2 && m1 < maxn) lbase[slot1] = e2;
+                mycnt = s2 ? m2 : (s1 ? m1 : mycnt);
+                slot = s2 ? slot2 : (s1 ? slot1 : slot);
+                // round r used up: on to the next round with entries
+                const int rn = rest ? __ffs(rest) - 1 : 0;
+                const unsigned tn = s_t[w][rn][lane];
+                const bool more = t2 != 0u;
+                t = more ? t2 : (rest ? tn : 0u);
+                r = more ? r : rn;
+                rest = more ? rest : (rest & (rest - 1u));
             }
             __syncwarp();
             rb = 0;
@@ -648,13 +649,10 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
         };
         // one round: queue entries 0..cnt-1 (cnt <= 32), one per lane
         auto round = [&](int cnt) {
-            float qx = -1.0e18f, qy = -1.0e18f, qz = -1.0e18f;
-            uint32_t e = 0u;
-            if (lane < cnt) {
-                const float4 c = s_q[w][lane];
-                qx = c.x; qy = c.y; qz = c.z;
-                e = __float_as_uint(c.w);
-            }
+            const float4 cq = s_q[w][lane];
+            const bool qin = lane < cnt;
+            const float qx = qin ? cq.x : -1.0e18f, qy = qin ? cq.y : -1.0e18f, qz = qin ? cq.z : -1.0e18f;
+            const uint32_t e = qin ? __float_as_uint(cq.w) : 0u;
             // acceptance bits over the home atoms, 8 at a time with
             // compile-time bit positions.  t = |x_i - q|^2 - rl^2 in the
             // dot-product form |x_i|^2 + |q|^2 - 2 x_i.q (FP32 error
@@ -712,28 +710,29 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
             while (qn < 32 && row < 9) {
                 // this lane as a candidate, shifted into the home frame,
                 // kept if within rl (plus the band) of the home bounding box
+                // (lanes past the row's end read a valid record, the chunk's
+                // first home atom's, and are dropped: no branch)
                 const int f = c0 + lane;
-                bool keep = false;
+                const int2 ca = s_cell[w][3 * row], cb = s_cell[w][3 * row + 1];
+                const int cxs = s_cell[w][3 * row + 2].x;
+                const int nab = ca.y + cb.y;
+                const int seg = (f >= ca.y) + (f >= nab);
+                const int j0 = seg == 0 ? ca.x + f : (seg == 1 ? cb.x + f - ca.y : cxs + f - nab);
+                const bool in = f < m;
+                const int j = in ? j0 : hbase;
+                const float4 rj = V.rec[j];
+                const int dy = row % 3 - 1, dz = row / 3 - 1;
                 float4 c;
-                if (f < m) {
-                    const int dy = row % 3 - 1, dz = row / 3 - 1;
-                    const int2 c0_ = s_cell[w][3 * row], c1_ = s_cell[w][3 * row + 1];
-                    const int seg = (f >= c0_.y) + (f >= c0_.y + c1_.y);
-                    const int j = seg == 0 ? c0_.x + f
-                                           : (seg == 1 ? c1_.x + f - c0_.y
-                                                       : s_cell[w][3 * row + 2].x + f - c0_.y - c1_.y);
-                    const float4 rj = V.rec[j];
-                    c.x = rj.x + (seg - 1) * hx;
-                    c.y = rj.y + dy * hy;
-                    c.z = rj.z + dz * hz;
-                    c.w = __uint_as_float(((uint32_t)j << 6) | (uint32_t)seg | ((uint32_t)(dz + 1) << 4) |
-                                          ((uint32_t)(dy + 1) << 2));
-                    const float4 lo = s_box[w][0], hi = s_box[w][1];
-                    const float bx_ = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
-                    const float by_ = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
-                    const float bz_ = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
-                    keep = bx_ * bx_ + by_ * by_ + bz_ * bz_ < keep2;
-                }
+                c.x = rj.x + (seg == 0 ? -hx : (seg == 1 ? 0.f : hx));
+                c.y = rj.y + dy * hy;
+                c.z = rj.z + dz * hz;
+                c.w = __uint_as_float(((uint32_t)j << 6) | (uint32_t)seg | ((uint32_t)(dz + 1) << 4) |
+                                      ((uint32_t)(dy + 1) << 2));
+                const float4 lo = s_box[w][0], hi = s_box[w][1];
+                const float bx_ = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
+                const float by_ = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
+                const float bz_ = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
+                const bool keep = in && (bx_ * bx_ + by_ * by_ + bz_ * bz_ < keep2);
                 const unsigned kb = __ballot_sync(0xffffffffu, keep);
                 if (keep) s_q[w][qn + __popc(kb & ((1u << lane) - 1u))] = c;
                 qn += __popc(kb);
@@ -751,8 +750,7 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
             round(cnt);
             qn -= cnt;
             __syncwarp();
-            float4 rest;
-            if (lane < qn) rest = s_q[w][32 + lane];
+            const float4 rest = s_q[w][32 + lane];
             __syncwarp();
             if (lane < qn) s_q[w][lane] = rest;
             __syncwarp();
@@ -771,7 +769,7 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
 }
 
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build(View V, KArgs a) {
+__global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build(View V, KArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
     const int gw = blockIdx.x * kBuildWarps + w;
@@ -859,7 +857,7 @@ __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
 // Batched rebuild: a fixed grid walks the work list's units (k_worklist), so
 // that the bins of replicas keeping their lists cost no block launches.
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(32 * kBuildWarps, 32 / kBuildWarps) k_build_wl(View V, KArgs a) {
+__global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build_wl(View V, KArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nf = *V.wl_n;
     const int total = V.wl_u0[nf];
@@ -902,14 +900,14 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     as.wl = wl ? 1 : 0;
     const dim3 gs(wl ? (unsigned)(V.n_sm * 8) : (unsigned)((V.n_pad + 255) / 256));
     if (wl) seq.push_back(KCall{(const void *)k_worklist, dim3(1), dim3(1024), 0, a});
-    seq.push_back(KCall{(const void *)k_zero_bins, dim3(V.n_rep), dim3(256), 0, a});
+    const int nzb = (max(V.nbins_total, V.n_rep) + 255) / 256;
+    seq.push_back(KCall{(const void *)k_zero_bins, dim3((unsigned)min(nzb, V.n_sm * 8)), dim3(256), 0, a});
     KArgs ap = as;
     ap.mode = staged ? 1 : 0;
     seq.push_back(KCall{fp64 ? (const void *)k_prepare<MD_PREC_FP64> : (const void *)k_prepare<MD_PREC_MIXED>, gs,
                         dim3(256), 0, ap});
     const int nblk = (V.nbins_total + kScanBlock - 1) / kScanBlock;
     seq.push_back(KCall{(const void *)k_scan1, dim3(nblk), dim3(1024), 0, a});
-    seq.push_back(KCall{(const void *)k_scan2, dim3(1), dim3(1024), 0, a});
     seq.push_back(KCall{(const void *)k_scan3, dim3((V.nbins_total + 255) / 256), dim3(256), 0, a});
     seq.push_back(KCall{(const void *)k_scatter, gs, dim3(256), 0, as});
     seq.push_back(KCall{fp64 ? (const void *)k_gather<MD_PREC_FP64> : (const void *)k_gather<MD_PREC_MIXED>, gs,
@@ -919,7 +917,7 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     if (wl) {
         const void *kb = fp64 ? (V.half ? (const void *)k_build_wl<MD_PREC_FP64, 1> : (const void *)k_build_wl<MD_PREC_FP64, 0>)
                               : (V.half ? (const void *)k_build_wl<MD_PREC_MIXED, 1> : (const void *)k_build_wl<MD_PREC_MIXED, 0>);
-        seq.push_back(KCall{kb, dim3(V.n_sm * (32 / kBuildWarps)), dim3(32 * kBuildWarps), 0, a});
+        seq.push_back(KCall{kb, dim3(V.n_sm * kBuildBlocksPerSM), dim3(32 * kBuildWarps), 0, a});
         return;
     }
     const void *kb = fp64 ? (V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>)

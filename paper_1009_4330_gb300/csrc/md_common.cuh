@@ -75,6 +75,7 @@ struct Ctl {                // device control block of a handle
     long long steps;        // completed time steps
     long long rebuilds;     // completed replica builds
     unsigned disp_max;      // md_vv MD_VV_DISP: max squared displacement since the build, float bits
+    unsigned ticket_scan;   // last-block ticket of the bin-count scan's first pass (reset by the last block)
 };
 
 // Parameters of the potential, per ordered type pair p = ti * nt + tj.
