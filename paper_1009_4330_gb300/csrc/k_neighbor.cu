@@ -501,21 +501,24 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 // the FP64 definition exactly.  HALF keeps j > i only.
 constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
 constexpr int kBatch = 14;  // rounds whose list entries are appended together
-constexpr int kBuildWarps = 4;  // warps (cells or cell parts) per block
-// blocks per SM the list build is compiled for: 7 (72 registers, 28 warps)
-// measured faster than 8 (64 registers, more spills) on the 864,000-atom liquid
-constexpr int kBuildBlocksPerSM = 7;
+// The list build runs NW warps (cells or cell parts) per block, compiled for
+// 28 warps per SM (72 registers; 32 warps at 64 registers spilled inside the
+// loops).  One warp per block when every cell has one warp (no block
+// barrier, and a block's registers come free as soon as its cell is done;
+// the warp's shared-memory addresses are then constants); four when the
+// warps of a cell share it out, so that they share its candidates in L1.
+constexpr int kBuildWarpsPerSM = 28;
 
-template <int PREC, int HALF>
+template <int PREC, int HALF, int NW>
 __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int hsplit, int lane, int w,
                                            int &my_max, long long &my_sum) {
-    __shared__ float4 s_h[kBuildWarps][32];
-    __shared__ float4 s_q[kBuildWarps][kQueue];  // shifted candidate position, .w = list entry bits
-    __shared__ float4 s_box[kBuildWarps][2];     // bounding box of the home chunk: lo, hi
-    __shared__ int2 s_cell[kBuildWarps][27];     // neighbour cells: first slot, count
-    __shared__ int s_delta[kBuildWarps][2][64];     // per tile of the chunk, per stencil code: entry shift
-    __shared__ uint32_t s_t[kBuildWarps][kBatch][32];  // per round: home atom's mask of accepted candidates
-    __shared__ uint32_t s_e[kBuildWarps][kBatch][32];  // per round: candidate's list entry
+    __shared__ float4 s_h[NW][32];
+    __shared__ float4 s_q[NW][kQueue];  // shifted candidate position, .w = list entry bits
+    __shared__ float4 s_box[NW][2];     // bounding box of the home chunk: lo, hi
+    __shared__ int2 s_cell[NW][27];     // neighbour cells: first slot, count
+    __shared__ int s_delta[NW][2][64];     // per tile of the chunk, per stencil code: entry shift
+    __shared__ uint32_t s_t[NW][kBatch][32];  // per round: home atom's mask of accepted candidates
+    __shared__ uint32_t s_e[NW][kBatch][32];  // per round: candidate's list entry
     const int r = V.bin_rep[gb];
     const Rep &R = V.rep[r];
     const int maxn = V.maxneigh, lt = V.ltpa, lq = V.lvec;
@@ -768,11 +771,11 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
     }
 }
 
-template <int PREC, int HALF>
-__global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build(View V, KArgs a) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+template <int PREC, int HALF, int NW>
+__global__ void __launch_bounds__(32 * NW, kBuildWarpsPerSM / NW) k_build(View V, KArgs a) {
+    const int lane = threadIdx.x & 31, w = NW == 1 ? 0 : threadIdx.x >> 5;
     // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
-    const int gw = blockIdx.x * kBuildWarps + w;
+    const int gw = blockIdx.x * NW + w;
     const int gb = gw / V.hsplit, part = gw - gb * V.hsplit;
     int my_max = 0;
     long long my_sum = 0;
@@ -780,34 +783,16 @@ __global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build(V
     if (gb < V.nbins_total) {
         const int r = V.bin_rep[gb];
         my_rep = r;
-        if (a.all || V.rep_flag[r]) build_cell<PREC, HALF>(V, gb, part, V.hsplit, lane, w, my_max, my_sum);
+        if (a.all || V.rep_flag[r]) build_cell<PREC, HALF, NW>(V, gb, part, V.hsplit, lane, w, my_max, my_sum);
     }
-    // statistics per replica: warp max / sum, merged over the block's warps
-    // that belong to the same replica, one atomic per run
-    __shared__ int s_max[kBuildWarps], s_rep[kBuildWarps];
-    __shared__ long long s_sum[kBuildWarps];
+    // statistics per replica: one atomic pair per warp, no block barrier
     for (int o = 16; o > 0; o >>= 1) {
         my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
         my_sum += __shfl_xor_sync(0xffffffffu, my_sum, o);
     }
-    if (lane == 0) { s_max[w] = my_max; s_sum[w] = my_sum; s_rep[w] = my_rep; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int cr = -1, mm = 0;
-        long long ss = 0;
-        for (int k = 0; k <= (int)(blockDim.x >> 5); ++k) {
-            const bool end = (k == (int)(blockDim.x >> 5));
-            if (end || s_rep[k] != cr) {
-                if (cr >= 0 && ss > 0) {
-                    atomicMax(&V.rep_maxcnt[cr], mm);
-                    atomicAdd(&V.rep_entries[cr], (unsigned long long)ss);
-                }
-                if (end) break;
-                cr = s_rep[k]; mm = 0; ss = 0;
-            }
-            mm = max(mm, s_max[k]);
-            ss += s_sum[k];
-        }
+    if (lane == 0 && my_rep >= 0 && my_sum > 0) {
+        atomicMax(&V.rep_maxcnt[my_rep], my_max);
+        atomicAdd(&V.rep_entries[my_rep], (unsigned long long)my_sum);
     }
     // builds of every replica (creation, md_build_neighbors, md_set_state) are
     // counted here; the step's builds of flagged replicas were counted with the
@@ -857,11 +842,11 @@ __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
 // Batched rebuild: a fixed grid walks the work list's units (k_worklist), so
 // that the bins of replicas keeping their lists cost no block launches.
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build_wl(View V, KArgs a) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__global__ void __launch_bounds__(32, kBuildWarpsPerSM) k_build_wl(View V, KArgs a) {
+    const int lane = threadIdx.x & 31, w = 0;
     const int nf = *V.wl_n;
     const int total = V.wl_u0[nf];
-    for (int u = blockIdx.x * kBuildWarps + w; u < total; u += gridDim.x * kBuildWarps) {
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
         // the flagged replica holding unit u: the last f with wl_u0[f] <= u
         int lo = 0, hi = nf - 1;
         while (lo < hi) {
@@ -874,7 +859,7 @@ __global__ void __launch_bounds__(32 * kBuildWarps, kBuildBlocksPerSM) k_build_w
         const int gb = __ldg(&V.wl_bin[lo]) + local / hs, part = local % hs;
         int my_max = 0;
         long long my_sum = 0;
-        build_cell<PREC, HALF>(V, gb, part, hs, lane, w, my_max, my_sum);
+        build_cell<PREC, HALF, 1>(V, gb, part, hs, lane, w, my_max, my_sum);
         for (int o = 16; o > 0; o >>= 1) {
             my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
             my_sum += __shfl_xor_sync(0xffffffffu, my_sum, o);
@@ -917,12 +902,18 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     if (wl) {
         const void *kb = fp64 ? (V.half ? (const void *)k_build_wl<MD_PREC_FP64, 1> : (const void *)k_build_wl<MD_PREC_FP64, 0>)
                               : (V.half ? (const void *)k_build_wl<MD_PREC_MIXED, 1> : (const void *)k_build_wl<MD_PREC_MIXED, 0>);
-        seq.push_back(KCall{kb, dim3(V.n_sm * kBuildBlocksPerSM), dim3(32 * kBuildWarps), 0, a});
+        seq.push_back(KCall{kb, dim3(V.n_sm * kBuildWarpsPerSM), dim3(32), 0, a});
         return;
     }
-    const void *kb = fp64 ? (V.half ? (const void *)k_build<MD_PREC_FP64, 1> : (const void *)k_build<MD_PREC_FP64, 0>)
-                          : (V.half ? (const void *)k_build<MD_PREC_MIXED, 1> : (const void *)k_build<MD_PREC_MIXED, 0>);
-    seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + kBuildWarps - 1) / kBuildWarps), dim3(32 * kBuildWarps), 0, a});
+    const int nw = V.hsplit > 1 ? 4 : 1;
+    const void *kb;
+    if (nw == 1)
+        kb = fp64 ? (V.half ? (const void *)k_build<MD_PREC_FP64, 1, 1> : (const void *)k_build<MD_PREC_FP64, 0, 1>)
+                  : (V.half ? (const void *)k_build<MD_PREC_MIXED, 1, 1> : (const void *)k_build<MD_PREC_MIXED, 0, 1>);
+    else
+        kb = fp64 ? (V.half ? (const void *)k_build<MD_PREC_FP64, 1, 4> : (const void *)k_build<MD_PREC_FP64, 0, 4>)
+                  : (V.half ? (const void *)k_build<MD_PREC_MIXED, 1, 4> : (const void *)k_build<MD_PREC_MIXED, 0, 4>);
+    seq.push_back(KCall{kb, dim3((V.nbins_total * V.hsplit + nw - 1) / nw), dim3(32 * nw), 0, a});
 }
 
 }  // namespace md
