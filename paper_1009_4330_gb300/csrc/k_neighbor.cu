@@ -501,13 +501,17 @@ __device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
 // the FP64 definition exactly.  HALF keeps j > i only.
 constexpr int kQueue = 64;  // queued candidates per warp (< 32 left + 32 new)
 constexpr int kBatch = 14;  // rounds whose list entries are appended together
-// The list build runs NW warps (cells or cell parts) per block, compiled for
-// 28 warps per SM (72 registers; 32 warps at 64 registers spilled inside the
-// loops).  One warp per block when every cell has one warp (no block
-// barrier, and a block's registers come free as soon as its cell is done;
-// the warp's shared-memory addresses are then constants); four when the
-// warps of a cell share it out, so that they share its candidates in L1.
-constexpr int kBuildWarpsPerSM = 28;
+// The list build runs NW warps (cells or cell parts) per block.  One warp
+// per block when every cell has one warp: no block barrier, a block's
+// registers come free as soon as its cell is done, and the warp's
+// shared-memory addresses are constants, so that 64 registers (32 warps per
+// SM) hold the loops without spills.  Four when the warps of a cell share it
+// out, so that they share its candidates in L1; compiled for 28 warps per
+// SM (72 registers: at 64 this form spilled inside the loops).
+template <int NW>
+struct BuildOcc {
+    static constexpr int warps_per_sm = NW == 1 ? 32 : 28;
+};
 
 template <int PREC, int HALF, int NW>
 __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int hsplit, int lane, int w,
@@ -772,7 +776,7 @@ __device__ __forceinline__ void build_cell(const View &V, int gb, int part, int 
 }
 
 template <int PREC, int HALF, int NW>
-__global__ void __launch_bounds__(32 * NW, kBuildWarpsPerSM / NW) k_build(View V, KArgs a) {
+__global__ void __launch_bounds__(32 * NW, BuildOcc<NW>::warps_per_sm / NW) k_build(View V, KArgs a) {
     const int lane = threadIdx.x & 31, w = NW == 1 ? 0 : threadIdx.x >> 5;
     // warp -> (cell, part): part q of a cell takes its home chunks q, q + hsplit, ...
     const int gw = blockIdx.x * NW + w;
@@ -842,7 +846,7 @@ __global__ void __launch_bounds__(1024) k_worklist(View V, KArgs a) {
 // Batched rebuild: a fixed grid walks the work list's units (k_worklist), so
 // that the bins of replicas keeping their lists cost no block launches.
 template <int PREC, int HALF>
-__global__ void __launch_bounds__(32, kBuildWarpsPerSM) k_build_wl(View V, KArgs a) {
+__global__ void __launch_bounds__(32, BuildOcc<1>::warps_per_sm) k_build_wl(View V, KArgs a) {
     const int lane = threadIdx.x & 31, w = 0;
     const int nf = *V.wl_n;
     const int total = V.wl_u0[nf];
@@ -902,7 +906,7 @@ void rebuild_sequence(const View &V, bool all, bool staged, std::vector<KCall> &
     if (wl) {
         const void *kb = fp64 ? (V.half ? (const void *)k_build_wl<MD_PREC_FP64, 1> : (const void *)k_build_wl<MD_PREC_FP64, 0>)
                               : (V.half ? (const void *)k_build_wl<MD_PREC_MIXED, 1> : (const void *)k_build_wl<MD_PREC_MIXED, 0>);
-        seq.push_back(KCall{kb, dim3(V.n_sm * kBuildWarpsPerSM), dim3(32), 0, a});
+        seq.push_back(KCall{kb, dim3(V.n_sm * BuildOcc<1>::warps_per_sm), dim3(32), 0, a});
         return;
     }
     const int nw = V.hsplit > 1 ? 4 : 1;
