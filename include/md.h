@@ -61,8 +61,8 @@ typedef enum {
     MD_ERR_BOX_TOO_SMALL = 4,  /* a box edge < 2 (cutoff + skin)                        */
     MD_ERR_LIST_OVERFLOW = 5,  /* neighbour capacity exceeded and growing it failed     */
     MD_ERR_NONFINITE = 6,      /* a position, velocity or force became NaN/Inf          */
-    MD_ERR_TIMEOUT = 7,        /* reserved: no kernel of this build waits on another    */
-    MD_ERR_UNSUPPORTED = 8     /* valid request outside this build's limits             */
+    MD_ERR_TIMEOUT = 7,        /* reserved: no kernel of this library waits on another  */
+    MD_ERR_UNSUPPORTED = 8     /* valid request outside this library's limits           */
 } md_status;
 
 typedef enum { MD_POT_LJ = 0, MD_POT_EAM_FS = 1 } md_potential;

@@ -259,6 +259,7 @@ struct LJPair {
     Acc ax, ay, az, e;
     Acc w[6];
     real rx, ry, rz;  // this round's plain partial sums
+    real re, rw[6];   // and of the energy and virial terms (EV)
     __device__ __forceinline__ bool in_cut(real r2) {
         if constexpr (PREC == MD_PREC_MIXED) {
             const real t = r2 - rc2;  // t < 0 exactly when r2 < rc2
@@ -267,8 +268,31 @@ struct LJPair {
         }
         return r2 < rc2;
     }
-    __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
-    __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
+    __device__ __forceinline__ void round_begin() {
+        rx = 0; ry = 0; rz = 0;
+        if (EV && PREC == MD_PREC_MIXED) {
+            re = 0;
+            for (int k = 0; k < 6; ++k) rw[k] = 0;
+        }
+    }
+    __device__ __forceinline__ void round_end() {
+        ax.add(rx); ay.add(ry); az.add(rz);
+        if (EV && PREC == MD_PREC_MIXED) {
+            e.add(re);
+            for (int k = 0; k < 6; ++k) w[k].add(rw[k]);
+        }
+    }
+    // energy and virial terms of one pair: summed plainly over the round and
+    // added with compensation per round (mixed), or added directly (FP64)
+    __device__ __forceinline__ void add_ev(real ee, real w0, real w1, real w2, real w3, real w4, real w5) {
+        if constexpr (PREC == MD_PREC_MIXED) {
+            re += ee;
+            rw[0] += w0; rw[1] += w1; rw[2] += w2; rw[3] += w3; rw[4] += w4; rw[5] += w5;
+        } else {
+            e.add(ee);
+            w[0].add(w0); w[1].add(w1); w[2].add(w2); w[3].add(w3); w[4].add(w4); w[5].add(w5);
+        }
+    }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int tj) {
         // mixed full list, forces only: branch-free (the skin entries' terms are
         // computed, finite since r2 >= rc^2 there, and zeroed) -- measured faster
@@ -299,9 +323,8 @@ struct LJPair {
             }
             if (EV) {
                 const real wgt = HALF ? (real)1 : (real)0.5;
-                e.add(wgt * (r6i * (lj3[tp] * r6i - lj4[tp]) - off[tp]));
-                w[0].add(wgt * dx * fxp); w[1].add(wgt * dy * fyp); w[2].add(wgt * dz * fzp);
-                w[3].add(wgt * dx * fyp); w[4].add(wgt * dx * fzp); w[5].add(wgt * dy * fzp);
+                add_ev(wgt * (r6i * (lj3[tp] * r6i - lj4[tp]) - off[tp]), wgt * dx * fxp, wgt * dy * fyp,
+                       wgt * dz * fzp, wgt * dx * fyp, wgt * dx * fzp, wgt * dy * fzp);
             }
         }
     }
@@ -775,9 +798,33 @@ struct EamPair {
     real rc, rc2, c0, c1, c2, fpi;
     Acc ax, ay, az, e;
     Acc w[6];
-    real rx, ry, rz;
-    __device__ __forceinline__ void round_begin() { rx = 0; ry = 0; rz = 0; }
-    __device__ __forceinline__ void round_end() { ax.add(rx); ay.add(ry); az.add(rz); }
+    real rx, ry, rz;  // this round's plain partial sums
+    real re, rw[6];   // and of the energy and virial terms (EV)
+    __device__ __forceinline__ void round_begin() {
+        rx = 0; ry = 0; rz = 0;
+        if (EV && PREC == MD_PREC_MIXED) {
+            re = 0;
+            for (int k = 0; k < 6; ++k) rw[k] = 0;
+        }
+    }
+    __device__ __forceinline__ void round_end() {
+        ax.add(rx); ay.add(ry); az.add(rz);
+        if (EV && PREC == MD_PREC_MIXED) {
+            e.add(re);
+            for (int k = 0; k < 6; ++k) w[k].add(rw[k]);
+        }
+    }
+    // energy and virial terms of one pair: summed plainly over the round and
+    // added with compensation per round (mixed), or added directly (FP64)
+    __device__ __forceinline__ void add_ev(real ee, real w0, real w1, real w2, real w3, real w4, real w5) {
+        if constexpr (PREC == MD_PREC_MIXED) {
+            re += ee;
+            rw[0] += w0; rw[1] += w1; rw[2] += w2; rw[3] += w3; rw[4] += w4; rw[5] += w5;
+        } else {
+            e.add(ee);
+            w[0].add(w0); w[1].add(w1); w[2].add(w2); w[3].add(w3); w[4].add(w4); w[5].add(w5);
+        }
+    }
     __device__ __forceinline__ void operator()(uint32_t ent, real dx, real dy, real dz, real r2, int wj) {
         if constexpr (PREC == MD_PREC_MIXED && !EV) {  // branch-free: t = 0 beyond rc zeroes the term
             const real fpj = (real)__int_as_float(wj);
@@ -803,9 +850,9 @@ struct EamPair {
             const real fxp = dx * coef, fyp = dy * coef, fzp = dz * coef;
             rx += fxp; ry += fyp; rz += fzp;
             if (EV) {
-                e.add((real)0.5 * t * t * poly);
-                w[0].add((real)0.5 * dx * fxp); w[1].add((real)0.5 * dy * fyp); w[2].add((real)0.5 * dz * fzp);
-                w[3].add((real)0.5 * dx * fyp); w[4].add((real)0.5 * dx * fzp); w[5].add((real)0.5 * dy * fzp);
+                const real h = (real)0.5;
+                add_ev(h * t * t * poly, h * dx * fxp, h * dy * fyp, h * dz * fzp, h * dx * fyp, h * dx * fzp,
+                       h * dy * fzp);
             }
         }
     }

@@ -88,7 +88,10 @@ __global__ void k_state_out(View V, double *x, double *v, double *f) {
 // ------------------------------------------------------ energy / virial ----
 
 // Two fixed-order stages: per 32-atom tile (one warp each), then per
-// replica over its tiles in order (one block each).
+// replica over its tiles (one block each, each thread a fixed stride of
+// tiles, then the block's fixed-order sum).  The tile stage loads its eight
+// terms before the eight shuffle trees, the replica stage reads each tile's
+// eight sums together: both are bound by memory, not by chains of waits.
 __global__ void k_ev_tiles(View V) {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -96,21 +99,40 @@ __global__ void k_ev_tiles(View V) {
     const int p = t * 32 + lane;
     const Rep &R = V.rep[V.tile_rep[t]];
     const bool ok = (p - R.atom0) < R.natoms;
-    for (int k = 0; k < 8; ++k) {
-        double x = ok ? V.ev[k * V.n_pad + p] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) V.ev_tile[(size_t)t * 8 + k] = x;
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = ok ? V.ev[k * V.n_pad + p] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+    if (lane < 8) {
+        double y = x[0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) y = lane == k ? x[k] : y;
+        V.ev_tile[(size_t)t * 8 + lane] = y;
     }
 }
 
-__global__ void k_ev_reduce(View V, double *out) {
+__global__ void __launch_bounds__(1024) k_ev_reduce(View V, double *out) {
     __shared__ double s_w[32];
     const int r = blockIdx.x;
     const Rep &R = V.rep[r];
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (int t = R.tile0 + threadIdx.x; t < R.tile0 + R.ntiles; t += blockDim.x) {
+        const double2 *q = reinterpret_cast<const double2 *>(&V.ev_tile[(size_t)t * 8]);
+        double2 u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[k] = q[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k] += u[k].x;
+            acc[2 * k + 1] += u[k].y;
+        }
+    }
     for (int k = 0; k < 8; ++k) {
-        double acc = 0.0;
-        for (int t = R.tile0 + threadIdx.x; t < R.tile0 + R.ntiles; t += blockDim.x) acc += V.ev_tile[(size_t)t * 8 + k];
-        const double tot = block_sum(acc, s_w);
+        const double tot = block_sum(acc[k], s_w);
         if (threadIdx.x == 0) out[8 * r + k] = tot;
     }
 }
@@ -594,7 +616,7 @@ cudaError_t launch_state_out(const View &V, double *x, double *v, double *f, cud
 
 cudaError_t launch_ev_reduce(const View &V, double *out, cudaStream_t s) {
     k_ev_tiles<<<grid_of(V.n_tiles * 32, 256), 256, 0, s>>>(V);
-    k_ev_reduce<<<V.n_rep, 256, 0, s>>>(V, out);
+    k_ev_reduce<<<V.n_rep, 1024, 0, s>>>(V, out);
     return cudaGetLastError();
 }
 
