@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     using real = typename P::real;
     extern __shared__ float4 s_rec[];
     const int tmode = begin_tile<PREC>(V, T, s_rec);
-    __syncthreads();
+    if (V.tile_atoms != 0) __syncthreads();  // only a staging block has shared state
     const unsigned err = V.ctl->err;
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31;
@@ -862,11 +862,12 @@ template <int PREC, int T, int Q, int EV>
 __global__ void __launch_bounds__(256) k_eam_force(View V, KArgs a) {
     using P = Pol<PREC>;
     using real = typename P::real;
-    __shared__ double s_ftm[kMaxTypes];
-    if (threadIdx.x < kMaxTypes) s_ftm[threadIdx.x] = V.tab->ftm_m[threadIdx.x];
+    // single element: ftm2v/m is read where it is used, no table to stage, so
+    // no block barrier either unless the block stages records
+    const double *s_ftm = V.tab->ftm_m;
     extern __shared__ float4 s_rec[];
     const int tmode = begin_tile<PREC>(V, T, s_rec);
-    __syncthreads();
+    if (V.tile_atoms != 0) __syncthreads();
     const unsigned err = V.ctl->err;
     const int rem = (a.mode == kModeStep) ? V.ctl->remaining : 0;
     constexpr int A = 32 / T;
