@@ -49,13 +49,15 @@ def parse():
     ap.add_argument("--block", type=int, default=128, help="force-kernel threads per block when --tpa is given")
     ap.add_argument("--eager", action="store_true",
                     help="step without CUDA graphs (kernels launched one by one; for profilers)")
-    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch", "lj4000", "force"],
+    ap.add_argument("--profile", default=None, choices=["build", "eam_backward", "batch", "lj4000", "force", "eam"],
                     help="run one small workload for a profiler and exit: 'build' = LJ liquid (--cells, --rc), "
                          "100 steps to melt the lattice, then two list rebuilds; 'eam_backward' = EAM metal "
                          "(--cells), forces + backward twice; 'lj4000' = the 4,000-atom FP64 liquid, 100 steps "
                          "in one md_step graph launch and 100 eager steps (kernels launched one by one), both "
                          "timed; 'force' = LJ liquid (--cells), mixed, one thread per atom, full list: 50 steps, "
-                         "then the force pass and its memory-only twin, each launched twice")
+                         "then the force pass and its memory-only twin, each launched twice; 'eam' = EAM metal "
+                         "(--cells), mixed, one thread per atom, full list: 100 steps, then the two force passes "
+                         "(density and force) launched twice")
     ap.add_argument("--rc", type=float, default=2.5, help="LJ cut-off of --profile build")
     return ap.parse_args()
 
@@ -780,6 +782,16 @@ def run_profile(args):
         print(json.dumps({"ms_per_step_graph": ms_graph / 100, "ms_per_step_eager": ms_eager / 100,
                           "rebuilds_graph": i1["rebuilds"] - i0["rebuilds"], "rebuilds_eager": j1["rebuilds"] - j0["rebuilds"],
                           "info": i1}))
+        s.close()
+        return
+    if args.profile == "eam":
+        e = synth.config2(cells=args.cells)
+        s = System.eam(e["x"], e["v"], e["box"], eam_params=e["eam"], skin=e["skin"], dt=e["dt"], mass=e["mass"],
+                       ftm2v=e["ftm2v"], precision="mixed", tpa=1, list="full")
+        s.set_kernel(1, "full", 128, 4)
+        s.step(100)
+        f_ms, _ = s.time_force(0, 2)
+        print(json.dumps({"force_ms": f_ms, "atoms": int(e["x"].shape[0])}))
         s.close()
         return
     if args.profile == "force":
