@@ -775,17 +775,20 @@ __global__ void __launch_bounds__(256) k_eam_rho(View V, KArgs a) {
     const double rho = group_sum<T>(pr.acc.value());
     if (valid && sub == 0) {
         const double Aemb = V.tab->eam[1];
-        const double sr = sqrt(rho);
-        const double fpv = rho > 0.0 ? -0.5 * Aemb / sr : 0.0;
         if (PREC == MD_PREC_FP64) {
-            V.fp64[p] = fpv;
+            const double sr = sqrt(rho);
+            V.fp64[p] = rho > 0.0 ? -0.5 * Aemb / sr : 0.0;
         } else {
             // single element: the record's type slot is free until the next drift
             // rewrites it, so F'(rho) rides in rec.w and the force pass gathers
-            // one 16-byte record per pair instead of two separate loads
-            V.rec[p].w = (float)fpv;
+            // one 16-byte record per pair instead of two separate loads.  It is
+            // stored as FP32, so it is formed in FP32 (one reciprocal square
+            // root, a few FP32 ulps) rather than by an FP64 square root and
+            // divide on the FP64 pipe for every atom
+            const float rf = (float)rho;
+            V.rec[p].w = rf > 0.f ? -0.5f * (float)Aemb * rsqrtf(rf) : 0.f;
         }
-        if (a.mode == kModeEV) V.emb[p] = rho > 0.0 ? -Aemb * sr : 0.0;
+        if (a.mode == kModeEV) V.emb[p] = rho > 0.0 ? -Aemb * sqrt(rho) : 0.0;
     }
 }
 
