@@ -478,7 +478,7 @@ __global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, 
     for (int k = 0; k < 6; ++k) pr.w[k].zero();
     bool valid = false;
     if (warp_in) {
-        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        const Rep &R = V.rep[V.n_rep == 1 ? 0 : V.tile_rep[p >> 5]];  // one replica: no lookup
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
             const int cnt = V.ncount[p];
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_probe(View V, KArgs a) {
     pr.acc = 0.f;
     bool valid = false;
     if (gw * A < V.n_pad && tmode >= 0) {
-        const Rep &R = V.rep[V.tile_rep[p >> 5]];
+        const Rep &R = V.rep[V.n_rep == 1 ? 0 : V.tile_rep[p >> 5]];  // one replica: no lookup
         valid = (p - R.atom0) < R.natoms;
         if (valid) {
             const int cnt = V.ncount[p];
@@ -973,7 +973,7 @@ __device__ __forceinline__ float drift_one(const View &V, int p, int first, int 
 // which is left untouched.  Returns the larger squared displacement.
 __device__ __forceinline__ float drift_pair(const View &V, int p, int first, int &rep) {
     const int n = V.n_pad;
-    rep = V.tile_rep[p >> 5];
+    rep = V.n_rep == 1 ? 0 : V.tile_rep[p >> 5];
     const Rep &R = V.rep[rep];
     const int l0 = p - R.atom0;
     if (l0 >= R.natoms) return 0.f;
