@@ -360,7 +360,7 @@ def run_reference(args, ws, rank):
 # 500,000-atom case of this workload, scaled by atoms (the list length per
 # atom is the same).  Valid only for this kernel variant, as captured; for
 # any other variant roofline.traffic is null.
-K_LJ_TRAFFIC_PER_ATOM = (182.565120e6 + 4.033024e6) / 500000
+K_LJ_TRAFFIC_PER_ATOM = (182.529792e6 + 3.975168e6) / 500000
 K_LJ_TRAFFIC_VARIANT = {"tpa": 1, "vec": 4, "list": "full", "block": 128, "tile_atoms": 0}
 
 # FP32 operations per list entry of the mixed full-list pair loop (a fused
