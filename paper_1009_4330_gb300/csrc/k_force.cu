@@ -8,13 +8,15 @@
 // ..., gathers j's record, evaluates the pair term and accumulates; the group
 // then reduces its partial sums with warp shuffles (the paper's reduce(ftmp)
 // of the block-per-atom listing) and one thread writes atom i.
-// Per-type coefficient tables are staged in shared memory.
+// Per-type coefficient tables are staged in shared memory; with one atom
+// type the two coefficients are held in registers and nothing is staged.
 //
 // Precision (paper Sec. II, mixed mode: force in single, integration in
 // double): MIXED gathers FP32 cell-relative records, does the pair
-// arithmetic in FP32, accumulates each thread's partial sums with Kahan
-// compensation and folds them into FP64 for the group reduction, kick and
-// store.  FP64 does everything in double.
+// arithmetic in FP32, sums each round's (at most Q) pair terms plainly and
+// adds the round sum with Kahan compensation (forces, energy and virial
+// alike), and folds the compensated sums into FP64 for the group reduction,
+// kick and store.  FP64 does everything in double.
 #include "md_common.cuh"
 #include "md_kernels.h"
 
