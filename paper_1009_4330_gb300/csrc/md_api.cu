@@ -7,13 +7,14 @@
 // md_step graph (built once per handle configuration, replayed per call):
 //
 //   k_loop_init --> WHILE(cond_loop) {
-//       k_drift --> IF(cond_rebuild) { zero bins, prepare, scan, scatter,
-//                                      gather, build } --> force pass(es)
+//       k_drift --> k_drift_done --> IF(cond_rebuild) { zero bins, prepare,
+//           scan, scatter, gather, build } --> force pass(es)
 //   }
 //
-// k_drift's last block sets cond_rebuild from the per-replica displacement
-// check, counts the step, decrements the remaining step count and sets
-// cond_loop; the force pass takes no ticket.  No host round trip per step.
+// k_drift_done (one block) sets cond_rebuild from the per-replica
+// displacement check, counts the step, decrements the remaining step count
+// and sets cond_loop; neither the drift nor the force pass takes a ticket.
+// No host round trip per step.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
