@@ -253,6 +253,7 @@ struct LJPair {
     using Acc = typename Pol<PREC>::Acc;
     const View *V;
     const real *lj1, *lj2, *lj3, *lj4, *off;
+    real c3, c4, c0;  // one atom type: the energy coefficients and shift, likewise
     real c1, c2;  // one atom type (MT = 0): the coefficients in registers, not
                   // re-read from shared memory for every pair
     real rc2;
@@ -309,6 +310,21 @@ struct LJPair {
             rx += dx * fpair; ry += dy * fpair; rz += dz * fpair;
             return;
         }
+        // mixed full list, one atom type, with energy and virial: branch-free
+        // as well (a zero force term zeroes the virial terms; the energy term
+        // is selected)
+        if constexpr (!HALF && EV && !MT && PREC == MD_PREC_MIXED) {
+            const real r2i = Pol<PREC>::rcp(r2);
+            const real r6i = r2i * r2i * r2i;
+            const bool in = in_cut(r2);
+            const real fpair = in ? r6i * (c1 * r6i - c2) * r2i : (real)0;
+            const real fxp = dx * fpair, fyp = dy * fpair, fzp = dz * fpair;
+            rx += fxp; ry += fyp; rz += fzp;
+            const real h = (real)0.5;
+            add_ev(in ? h * (r6i * (c3 * r6i - c4) - c0) : (real)0, h * dx * fxp, h * dy * fyp, h * dz * fzp,
+                   h * dx * fyp, h * dx * fzp, h * dy * fzp);
+            return;
+        }
         if (in_cut(r2)) {
             const int tp = MT ? ti * nt + tj : 0;
             const real r2i = Pol<PREC>::rcp(r2);
@@ -325,7 +341,8 @@ struct LJPair {
             }
             if (EV) {
                 const real wgt = HALF ? (real)1 : (real)0.5;
-                add_ev(wgt * (r6i * (lj3[tp] * r6i - lj4[tp]) - off[tp]), wgt * dx * fxp, wgt * dy * fyp,
+                const real a3 = MT ? lj3[tp] : c3, a4 = MT ? lj4[tp] : c4, a0 = MT ? off[tp] : c0;
+                add_ev(wgt * (r6i * (a3 * r6i - a4) - a0), wgt * dx * fxp, wgt * dy * fyp,
                        wgt * dz * fzp, wgt * dx * fyp, wgt * dx * fzp, wgt * dy * fzp);
             }
         }
@@ -391,7 +408,8 @@ __device__ __forceinline__ void fix_near_warp(const View &V, LJPair<MD_PREC_MIXE
             }
             if (EV) {
                 const float wgt = HALF ? 1.f : 0.5f;
-                ce += sgn * wgt * (r6i * (pr.lj3[tp] * r6i - pr.lj4[tp]) - pr.off[tp]);
+                const float a3 = MT ? pr.lj3[tp] : pr.c3, a4 = MT ? pr.lj4[tp] : pr.c4, a0 = MT ? pr.off[tp] : pr.c0;
+                ce += sgn * wgt * (r6i * (a3 * r6i - a4) - a0);
                 cw[0] += wgt * dx * fxp; cw[1] += wgt * dy * fyp; cw[2] += wgt * dz * fzp;
                 cw[3] += wgt * dx * fyp; cw[4] += wgt * dx * fzp; cw[5] += wgt * dy * fzp;
             }
@@ -417,12 +435,15 @@ __device__ __forceinline__ void fix_near_warp(const View &V, LJPair<MD_PREC_MIXE
 
 // registers per thread allowed to the mixed force-only pass: 56 keeps nine
 // 128-thread blocks (36 warps) resident per SM to hide the gather latency;
-// groups of 8+ threads and half lists with 4-entry loads take 64 (no spills),
-// the FP64 and energy/virial variants what they need
+// groups of 8+ threads and half lists with 4-entry loads take 64 (no spills);
+// the mixed full-list energy/virial pass 80 (six blocks instead of five, no
+// spills: 0.39 -> 0.37 ms per md_energy_virial on the 864,000-atom liquid);
+// FP64 and the half-list energy pass what they need
 template <int PREC, int T, int Q, int HALF, int EV>
 struct LjRegs {
     static constexpr int value =
-        (PREC == MD_PREC_MIXED && !EV) ? (Q == 4 && (T > 4 || HALF) ? 64 : 56) : 255;
+        (PREC == MD_PREC_MIXED && !EV) ? (Q == 4 && (T > 4 || HALF) ? 64 : 56)
+                                       : ((PREC == MD_PREC_MIXED && !HALF) ? 80 : 255);
 };
 
 template <int PREC, int T, int Q, int HALF, int EV, int MT>
@@ -432,11 +453,11 @@ __global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, 
     __shared__ real s_lj1[kMaxTypes * kMaxTypes], s_lj2[kMaxTypes * kMaxTypes];
     __shared__ real s_lj3[kMaxTypes * kMaxTypes], s_lj4[kMaxTypes * kMaxTypes], s_off[kMaxTypes * kMaxTypes];
     __shared__ double s_ftm_sh[kMaxTypes];
-    // one atom type and no energies: no table to stage, so no block barrier
-    // either (unless the block stages records); the two coefficients and
-    // ftm2v/m are read into registers (-2.1 us per step on the 864,000-atom
-    // liquid against staging them)
-    constexpr bool kRegOnly = (MT == 0 && EV == 0);
+    // one atom type: no table to stage, so no block barrier either (unless
+    // the block stages records); the coefficients and ftm2v/m are read into
+    // registers (-2.1 us per step on the 864,000-atom liquid against staging
+    // them)
+    constexpr bool kRegOnly = (MT == 0);
     const double *s_ftm = kRegOnly ? V.tab->ftm_m : s_ftm_sh;
     const int np = kRegOnly ? 0 : V.ntypes * V.ntypes;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -468,6 +489,11 @@ __global__ void __maxnreg__((LjRegs<PREC, T, Q, HALF, EV>::value)) k_lj(View V, 
     if (kRegOnly) {
         pr.c1 = (PREC == MD_PREC_FP64) ? (real)V.tab->lj1[0] : (real)V.tab->lj1f[0];
         pr.c2 = (PREC == MD_PREC_FP64) ? (real)V.tab->lj2[0] : (real)V.tab->lj2f[0];
+        if (EV) {
+            pr.c3 = (PREC == MD_PREC_FP64) ? (real)V.tab->lj3[0] : (real)V.tab->lj3f[0];
+            pr.c4 = (PREC == MD_PREC_FP64) ? (real)V.tab->lj4[0] : (real)V.tab->lj4f[0];
+            pr.c0 = (PREC == MD_PREC_FP64) ? (real)V.tab->off[0] : (real)V.tab->offf[0];
+        }
     } else {
         pr.c1 = s_lj1[0]; pr.c2 = s_lj2[0];
     }
